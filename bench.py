@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the CDBM hot path on GB300.
+
+Workload: the Taylor-Green vortex on a periodic 4096 x 4096 grid (Sec. 3.5 setup
+scaled up: L = 0.05, U0 = 0.01, tau = 1e-4, dt = 5e-6, I = 3, velocity set
+(0.2, 0.2, 2, 2) / (0, 5, 0, 2.6)), double precision.  One bench step is one
+Runge-Kutta time step over the whole grid (two fused stage kernels).  The state is
+2.15 GB per buffer, far above the 129 MB L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  Under torchrun every rank advances its own
+independent vortex (weak scaling, no data-path collective); the barrier and the
+max-over-ranks time use torch.distributed.
+
+--impl reference times the CPU oracle (test infrastructure) on a bounded sample
+of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s and HBM GB/s vs FP64 plain on same GB300 at stated L2 error"
+UNIT = "cell-updates/s"
+
+# FP64 work of the fused stage kernels per cell (counted from the kernel source;
+# an FMA counts as two flops).  Stage 1: 317 FP64 instructions / 442 flops;
+# stage 2: 333 / 474.  Bytes per cell-step: stage 1 reads f^n and writes f1
+# (128 + 128 B); stage 2 reads f1 and f^n and writes f^n+1 (384 B).
+FP64_INSTR_PER_CELL_STEP = 650
+FP64_FLOPS_PER_CELL_STEP = 916
+BYTES_PER_CELL_STEP = 640
+FP64_LANES_PER_CLK_PER_SM = 2       # 1.25 TFLOP/s nominal FP64 / (2 flops x 152 SMs x 2.07 GHz)
+
+# DRAM traffic of one stage launch (mean of the two stages) from one ncu capture of
+# the stage kernels; valid only while the kernel sources hash to TRAFFIC_SHA.
+# Captured at 1024^2 (134 MB per plane set, above L2) and scaled by 16 cells-fold; see
+# profiles/stage_kernel_tgv.md.
+TRAFFIC_SHA = "d051db640608e2e9"
+TRAFFIC_BYTES_PER_LAUNCH = 4.784e9
+
+
+def kernel_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2502_16818_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["cdbm", "reference"], default="cdbm")
+    p.add_argument("--n", type=int, default=4096, help="grid size (n x n)")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(n):
+    from paper_2502_16818_gb300 import workloads as W
+    return W.taylor_green(n=n, I=3.0)
+
+
+def cpu_sample(w, side):
+    """A side x side block of the workload's initial fields (zero-gradient edges)."""
+    import oracle
+    sub = [a[:side, :side] for a in (w.rho, w.ux, w.uy, w.T)]
+    m = oracle.Model(nx=side, ny=side, dx=w.dx, dy=w.dy, dt=w.dt, tau=w.tau, I=w.I, vg=w.vg,
+                     eg=w.eg, bc_x=1, bc_y=1, threads=os.cpu_count() or 1)
+    return m, sub
+
+
+def cpu_baseline(w, side=1024, steps=2):
+    """The oracle (as it stands) on the host cores: `steps` steps on a side^2 sample."""
+    import oracle
+    m, sub = cpu_sample(w, side)
+    f = oracle.init(m, *sub)
+    t0 = time.perf_counter()
+    oracle.step(m, f, steps)
+    dt = time.perf_counter() - t0
+    return {"value": side * side * steps / dt, "unit": UNIT, "cores": m.threads, "kind": "oracle",
+            "sample": "%dx%d block of the 4096^2 Taylor-Green initial state, %d RK2 steps, "
+                      "zero-gradient edges, %.1f s wall" % (side, side, steps, dt)}
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    w = workload(a.n)
+    import oracle
+    side = 512
+    m, sub = cpu_sample(w, side)
+    f = oracle.init(m, *sub)
+    for _ in range(a.warmup):
+        f = oracle.step(m, f, 1)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        f = oracle.step(m, f, 1)
+    dt = time.perf_counter() - t0
+    value = side * side * a.steps / dt
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3 / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "taylor_green_%dx%d_fp64" % (a.n, a.n), "sample": "%dx%d" % (side, side)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": m.threads, "kind": "oracle",
+                         "sample": "%dx%d block of the %d^2 Taylor-Green initial state, one RK2 step "
+                                   "per bench step" % (side, side, a.n)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_cdbm(a, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2502_16818_gb300 import Solver, cdbm
+
+    torch.cuda.set_device(local_rank)
+    w = workload(a.n)
+    cells = w.nx * w.ny
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = Solver.from_workload(w, stream=stream)
+        fields = [torch.from_numpy(x).to("cuda", non_blocking=False) for x in (w.rho, w.ux, w.uy, w.T)]
+        s.init(*fields)
+        s.step(a.warmup)
+    s.sync()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(a.steps)
+    e1.record(stream)
+    e1.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    s.sync()
+    torch.cuda.synchronize()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = cells * a.steps * world / (ms_max * 1e-3)
+
+    # roofline of the dominant kernels (the two fused stage kernels, ~100% of the step)
+    launch_ms = ms / (2 * a.steps)
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    peak_instr = FP64_LANES_PER_CLK_PER_SM * 152 * sm_mhz * 1e6
+    achieved_tflops = FP64_FLOPS_PER_CELL_STEP / 2 * cells / (launch_ms * 1e-3) / 1e12
+    peak_tflops = 2 * FP64_LANES_PER_CLK_PER_SM * 152 * 2070e6 / 1e12
+    instr_rate = FP64_INSTR_PER_CELL_STEP / 2 * cells / (launch_ms * 1e-3)
+    hbm_gbs = BYTES_PER_CELL_STEP * cells * a.steps / (ms * 1e-3) / 1e9
+    traffic = TRAFFIC_BYTES_PER_LAUNCH if TRAFFIC_SHA == kernel_sha() else None
+    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved_tflops / peak_tflops, "traffic": traffic,
+                "kernel": "stage_kernel (RK stages 1 and 2, mean per launch)",
+                "peak_source": "FP64 pipe: 2 lanes/clk/SM x 152 SMs x 2070 MHz x 2 flops (recipe nominal 1.25 TFLOP/s)",
+                "fp64_pipe_frac": instr_rate / peak_instr,
+                "hbm_gbs": hbm_gbs, "hbm_frac_of_measured": hbm_gbs / measured_hbm()}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "taylor_green_%dx%d_fp64" % (a.n, a.n), "nx": w.nx, "ny": w.ny,
+                   "I": w.I, "tau": w.tau, "dt": w.dt, "vset": [w.vg, w.eg], "precision": "fp64",
+                   "rk": "tvd2", "l2": "state 2.15 GB per buffer >> 129 MB L2, no flush",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "gpu_launches": 2 * a.steps,
+        "clocks": clocks,
+        "roofline": roofline,
+    }
+
+    if not a.no_e2e:
+        out["e2e"] = e2e(a, w, stream, cdbm, s, torch)
+    s.close()
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def e2e(a, w, stream, cdbm, s, torch):
+    """Same metric through the C ABI with host buffers: pinned host fields are
+    uploaded by cdbm_init, K steps run, and cdbm_macros downloads rho, u, T to
+    pinned host memory, all inside the timed region."""
+    host_in = [torch.from_numpy(x).pin_memory() for x in (w.rho, w.ux, w.uy, w.T)]
+    host_out = [torch.empty((w.ny, w.nx), dtype=torch.float64).pin_memory() for _ in range(4)]
+    cells = w.nx * w.ny
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    cdbm.cdbm_init(s.ctx, *(h.data_ptr() for h in host_in))
+    cdbm.cdbm_step(s.ctx, a.steps)
+    cdbm.cdbm_macros(s.ctx, *(h.data_ptr() for h in host_out))
+    e1.record(stream)
+    e1.synchronize()
+    wall = time.perf_counter() - t0
+    ms = max(e0.elapsed_time(e1), wall * 1e3)
+    cdbm.cdbm_sync(s.ctx)
+    nbytes = 4 * 8 * cells
+    return {"value": cells * a.steps / (ms * 1e-3), "unit": UNIT,
+            "h2d_bytes_per_step": nbytes / a.steps, "d2h_bytes_per_step": nbytes / a.steps,
+            "job": "upload rho,u,T -> cdbm_init -> %d steps -> cdbm_macros to host" % a.steps}
+
+
+def measured_hbm():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_cdbm(a, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

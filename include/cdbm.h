@@ -1,0 +1,182 @@
+/*
+ * cdbm.h -- C ABI of the GB300 central-moment discrete Boltzmann (CDBM) library.
+ *
+ * The library advances the 16 discrete velocity distributions f_i of the CDBM of
+ * Lin, Su, Fei and Luo ("Central-moment-based discrete Boltzmann modeling of
+ * compressible flows", Sec. 2) on a 2-D grid with hand-written CUDA kernels for
+ * sm_103a.  Each time step:
+ *   - forms rho, u, T from the conserved moments of f (Sec. 2, after Eq. 7);
+ *   - builds f_eq from the prescribed central moments of the Maxwellian with I
+ *     extra degrees of freedom (Eqs. 4-7);
+ *   - applies BGK relaxation and the NND/minmod transport term of every discrete
+ *     velocity (Eqs. 1, 12-20);
+ *   - runs two Runge-Kutta stages, one fused kernel each.
+ * On demand it extracts rho, u, T and the nonequilibrium quantities Delta*
+ * (Eqs. 8-11).
+ *
+ * Conventions shared by every entry point
+ *   - Discrete velocities (Eqs. 2-3): index i = 4g + k, group g = a, b, c, d.
+ *     Groups a and c point along the axes in the order (1,0),(0,1),(-1,0),(0,-1);
+ *     groups b and d along the diagonals in the order (1,1),(-1,1),(-1,-1),(1,-1);
+ *     each vector is scaled by its group speed (diagonals are not normalised).
+ *   - Fields are row-major [ny][nx] doubles (x fastest).  A distribution field is
+ *     [16][ny][nx] (velocity plane outermost).  Delta* is [12][ny][nx].
+ *   - D = 2; K = D + I; gamma = (K + 2) / K; T from rho K T = sum f((v-u)^2 + eta^2).
+ *   - Pointer arguments marked "host or device" may point to either kind of memory
+ *     (the library tells them apart through unified addressing); a host pointer is
+ *     staged through a library-owned device buffer.  Every other pointer is a
+ *     device pointer owned by the caller.
+ *   - All work is ordered on the context's CUDA stream and is asynchronous unless
+ *     an entry point says otherwise.
+ *   - Every entry point returns a cdbm_status and never aborts the process.  The
+ *     first error a context meets is sticky: later calls return it until the
+ *     context is destroyed; cdbm_last_error() gives a one-line description.
+ */
+#ifndef CDBM_H
+#define CDBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cdbm_ctx cdbm_ctx;
+
+typedef enum {
+    CDBM_OK = 0,
+    CDBM_EINVAL = 1,      /* bad argument (size, step, stability limit, pointer)   */
+    CDBM_ESINGULAR = 2,   /* the moment system of the velocity set is singular or  */
+                          /* worse conditioned than 1e12                           */
+    CDBM_ENOMEM = 3,      /* the allocator returned NULL                           */
+    CDBM_ECUDA = 4,       /* a CUDA runtime call failed                            */
+    CDBM_ENONPHYS = 5,    /* a kernel met rho <= 0, T <= 0 or a non-finite value   */
+    CDBM_ETIMEOUT = 6     /* a bounded device-side wait gave up                    */
+} cdbm_status;
+
+typedef enum { CDBM_BC_PERIODIC = 0, CDBM_BC_ZEROGRAD = 1 } cdbm_bc;
+
+/* Grid: nx, ny >= 1 cells of size dx, dy.  Boundary per axis: periodic, or
+ * zero-gradient (ghost cells repeat the edge cell).  The paper states no
+ * boundary condition; shock tubes use zero-gradient in x. */
+typedef struct {
+    int nx, ny;
+    double dx, dy;
+    int bc_x, bc_y;       /* cdbm_bc */
+} cdbm_grid;
+
+/* Discrete velocity set, Eqs. (2)-(3): group speeds (v_a, v_b, v_c, v_d) and
+ * extra-degree-of-freedom speeds (eta_a, eta_b, eta_c, eta_d). */
+typedef struct {
+    double v[4];
+    double eta[4];
+} cdbm_vset;
+
+/* Optional device-memory allocator (for example a caching allocator).  alloc
+ * returns device memory of at least `bytes` usable on `stream`, or NULL; free
+ * releases it.  With no allocator the library uses cudaMallocAsync/cudaFreeAsync
+ * on the context stream. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *user);
+    void *user;
+} cdbm_allocator;
+
+/* Precision of the stored state. */
+typedef enum {
+    CDBM_FP64 = 0         /* state, flux, equilibrium and sums in IEEE double      */
+} cdbm_precision;
+
+/* Time integrator.  The paper names a second-order Runge-Kutta scheme without
+ * printing it (Sec. 2): TVD is f1 = f + dt L(f), f <- (f + f1 + dt L(f1)) / 2;
+ * MIDPOINT is fh = f + dt/2 L(f), f <- f + dt L(fh). */
+typedef enum { CDBM_RK2_TVD = 0, CDBM_RK2_MIDPOINT = 1 } cdbm_rk;
+
+/*
+ * cdbm_create -- validates the run and builds a context (Sec. 2, Eqs. 1-7).
+ *   grid, vset   : see above (host memory, copied).
+ *   I            : extra degrees of freedom, I >= 0 (Eq. 5).
+ *   tau, dt      : relaxation time (Eq. 1) and time step, both > 0.
+ *   precision    : cdbm_precision.
+ *   cuda_stream  : cudaStream_t for all work of the context (NULL = legacy stream).
+ *   allocator    : NULL or a cdbm_allocator (copied).
+ *   out          : receives the context.
+ * The context owns the state f (two [16][ny][nx] buffers) and a few small
+ * scratch buffers; the state starts unset until cdbm_init or cdbm_set_state.
+ * Errors: CDBM_EINVAL for nx or ny < 1, dx, dy, dt, tau <= 0, I < 0 or non-finite
+ * input, a time step beyond the scheme's limits (max_i(|v_ix| dt/dx + |v_iy| dt/dy)
+ * > 1, or dt/tau > 2, outside the real stability interval of RK2); CDBM_ESINGULAR
+ * when the central-moment matrix at u = 0 (Eq. 6) is singular or has condition
+ * number above 1e12; CDBM_ENOMEM; CDBM_ECUDA.  On error *out is NULL.
+ */
+cdbm_status cdbm_create(const cdbm_grid *grid, const cdbm_vset *vset, double I, double tau,
+                        double dt, int precision, void *cuda_stream,
+                        const cdbm_allocator *allocator, cdbm_ctx **out);
+
+/* Chooses the Runge-Kutta variant (default CDBM_RK2_TVD). */
+cdbm_status cdbm_set_rk(cdbm_ctx *ctx, int rk);
+
+/*
+ * cdbm_init -- sets f = f_eq(rho, u, T) in every cell (Eqs. 5-7), time 0.
+ * rho, ux, uy, T: [ny][nx], host or device.
+ */
+cdbm_status cdbm_init(cdbm_ctx *ctx, const double *rho, const double *ux, const double *uy,
+                      const double *T);
+
+/*
+ * cdbm_step -- advances the state by nsteps >= 0 time steps of Eq. (1): per step two
+ * fused Runge-Kutta stage kernels (rho, u, T -> f_eq -> BGK + NND transport of all
+ * 16 velocities -> stage update).  Launches are replayed from a CUDA graph.
+ * Asynchronous; a non-physical state is reported by the next cdbm_sync.
+ */
+cdbm_status cdbm_step(cdbm_ctx *ctx, int nsteps);
+
+/*
+ * cdbm_macros -- writes rho, u_x, u_y, T of the current state ([ny][nx] each,
+ * host or device; a NULL pointer skips that field).  With any host pointer the
+ * call returns after the copy has finished.
+ */
+cdbm_status cdbm_macros(cdbm_ctx *ctx, double *rho, double *ux, double *uy, double *T);
+
+/*
+ * cdbm_tne -- nonequilibrium central moments of the current state, Eqs. (8)-(11):
+ * out[k][ny][nx], k = 0..11 = rows 5..16 of Eq. (6) applied to f - f_eq:
+ * Delta2 {xx, xy, yy}, Delta31 {x, y}, Delta3 {xxx, xxy, xyy, yyy},
+ * Delta42 {xx, xy, yy}.  out: host or device.
+ */
+cdbm_status cdbm_tne(cdbm_ctx *ctx, double *out);
+
+/*
+ * cdbm_conserved_sums -- domain totals of rho, rho u_x, rho u_y and
+ * sum_i f_i (v_i^2 + eta_i^2) (twice the total energy) into out[4] (host).
+ * Deterministic (fixed reduction order).  Synchronous.
+ */
+cdbm_status cdbm_conserved_sums(cdbm_ctx *ctx, double out[4]);
+
+/* Copies the state f ([16][ny][nx], host or device) and the time out / in. */
+cdbm_status cdbm_get_state(cdbm_ctx *ctx, double *f, double *t);
+cdbm_status cdbm_set_state(cdbm_ctx *ctx, const double *f, double t);
+
+/* Device pointer of the state f ([16][ny][nx] doubles, owned by the context,
+ * valid until cdbm_destroy); steps update it in place. */
+cdbm_status cdbm_state_ptr(cdbm_ctx *ctx, double **f);
+
+/* Simulated time (host scalar). */
+cdbm_status cdbm_time(const cdbm_ctx *ctx, double *t);
+
+/* Waits for the context stream and reports a sticky CUDA error or the
+ * device-side non-physical flag (CDBM_ENONPHYS). */
+cdbm_status cdbm_sync(cdbm_ctx *ctx);
+
+/* One-line description of the sticky error of ctx (NULL ctx: of the last failed
+ * cdbm_create on this thread).  Never NULL. */
+const char *cdbm_last_error(const cdbm_ctx *ctx);
+
+/* Releases the context and its device memory (stream-ordered).  NULL is a no-op. */
+void cdbm_destroy(cdbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CDBM_H */

@@ -58,29 +58,70 @@ class _Params(ctypes.Structure):
     ]
 
 
+def _configure(lib):
+    P = ctypes.POINTER(_Params)
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.orc_velocity_set.argtypes = [dp, dp, dp, dp, dp]
+    lib.orc_central_matrix.argtypes = [dp, dp, dp, ctypes.c_double, ctypes.c_double, dp]
+    lib.orc_central_moments_eq.argtypes = [ctypes.c_double] * 3 + [dp]
+    lib.orc_solve.argtypes = [ctypes.c_int, dp, dp, dp]
+    lib.orc_feq.argtypes = [P] + [ctypes.c_double] * 4 + [dp]
+    lib.orc_cell_macros.argtypes = [P, dp, dp, dp, dp, dp]
+    lib.orc_minmod.argtypes = [ctypes.c_double, ctypes.c_double]
+    lib.orc_minmod.restype = ctypes.c_double
+    lib.orc_nnd_derivative.argtypes = [ctypes.c_double, dp, ctypes.c_double]
+    lib.orc_nnd_derivative.restype = ctypes.c_double
+    lib.orc_init.argtypes = [P, dp, dp, dp, dp, dp]
+    lib.orc_step.argtypes = [P, dp, ctypes.c_int]
+    lib.orc_macros.argtypes = [P, dp, dp, dp, dp, dp]
+    lib.orc_tne.argtypes = [P, dp, dp]
+    lib.orc_conserved_sums.argtypes = [P, dp, dp]
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
-        P = ctypes.POINTER(_Params)
-        dp = ctypes.POINTER(ctypes.c_double)
-        lib.orc_velocity_set.argtypes = [dp, dp, dp, dp, dp]
-        lib.orc_central_matrix.argtypes = [dp, dp, dp, ctypes.c_double, ctypes.c_double, dp]
-        lib.orc_central_moments_eq.argtypes = [ctypes.c_double] * 3 + [dp]
-        lib.orc_solve.argtypes = [ctypes.c_int, dp, dp, dp]
-        lib.orc_feq.argtypes = [P] + [ctypes.c_double] * 4 + [dp]
-        lib.orc_cell_macros.argtypes = [P, dp, dp, dp, dp, dp]
-        lib.orc_minmod.argtypes = [ctypes.c_double, ctypes.c_double]
-        lib.orc_minmod.restype = ctypes.c_double
-        lib.orc_nnd_derivative.argtypes = [ctypes.c_double, dp, ctypes.c_double]
-        lib.orc_nnd_derivative.restype = ctypes.c_double
-        lib.orc_init.argtypes = [P, dp, dp, dp, dp, dp]
-        lib.orc_step.argtypes = [P, dp, ctypes.c_int]
-        lib.orc_macros.argtypes = [P, dp, dp, dp, dp, dp]
-        lib.orc_tne.argtypes = [P, dp, dp]
-        lib.orc_conserved_sums.argtypes = [P, dp, dp]
-        _lib = lib
+        _lib = _configure(ctypes.CDLL(build()))
     return _lib
+
+
+class use_library:
+    """Context manager that routes this module through another build of the oracle
+    source (used by the tests that plant mistakes in a copy of it)."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = _load()
+        _lib = _configure(ctypes.CDLL(self.path))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+def compile_variant(source_text: str, out_path: str) -> str:
+    """Compiles C source text with the oracle's flags into out_path (a .so)."""
+    src = out_path[:-3] + ".c"
+    with open(src, "w") as fh:
+        fh.write(source_text)
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
+            src, "-o", out_path, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    return out_path
+
+
+def source() -> str:
+    with open(_SRC) as fh:
+        return fh.read()
 
 
 def _ptr(a: np.ndarray):

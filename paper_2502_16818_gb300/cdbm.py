@@ -1,0 +1,305 @@
+"""ctypes binding of the C ABI in include/cdbm.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls; all arithmetic
+runs in the CUDA library ``_build/libcdbm.so``.  There is no CPU fallback:
+loading fails loudly when the library has not been built.
+
+``Solver`` wraps one context with PyTorch supplying device memory (through the
+caching allocator, passed to ``cdbm_create`` as callbacks) and the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+CDBM_OK, CDBM_EINVAL, CDBM_ESINGULAR, CDBM_ENOMEM, CDBM_ECUDA, CDBM_ENONPHYS, CDBM_ETIMEOUT = range(7)
+STATUS_NAMES = {0: "CDBM_OK", 1: "CDBM_EINVAL", 2: "CDBM_ESINGULAR", 3: "CDBM_ENOMEM",
+                4: "CDBM_ECUDA", 5: "CDBM_ENONPHYS", 6: "CDBM_ETIMEOUT"}
+CDBM_BC_PERIODIC, CDBM_BC_ZEROGRAD = 0, 1
+CDBM_FP64 = 0
+CDBM_RK2_TVD, CDBM_RK2_MIDPOINT = 0, 1
+
+#: every entry point declared in include/cdbm.h
+EXPORTS = ("cdbm_create", "cdbm_set_rk", "cdbm_init", "cdbm_step", "cdbm_macros", "cdbm_tne",
+           "cdbm_conserved_sums", "cdbm_get_state", "cdbm_set_state", "cdbm_state_ptr", "cdbm_time",
+           "cdbm_sync", "cdbm_last_error", "cdbm_destroy")
+
+
+class cdbm_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("dx", ctypes.c_double),
+                ("dy", ctypes.c_double), ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int)]
+
+
+class cdbm_vset(ctypes.Structure):
+    _fields_ = [("v", ctypes.c_double * 4), ("eta", ctypes.c_double * 4)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class cdbm_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", ctypes.c_void_p)]
+
+
+class CdbmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Loads libcdbm.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError("CUDA library %s is missing: build it with __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    ctx = ctypes.c_void_p
+    sig = {
+        "cdbm_create": ([ctypes.POINTER(cdbm_grid), ctypes.POINTER(cdbm_vset), ctypes.c_double,
+                         ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp,
+                         ctypes.POINTER(cdbm_allocator), ctypes.POINTER(ctx)], ctypes.c_int),
+        "cdbm_set_rk": ([ctx, ctypes.c_int], ctypes.c_int),
+        "cdbm_init": ([ctx, _vp, _vp, _vp, _vp], ctypes.c_int),
+        "cdbm_step": ([ctx, ctypes.c_int], ctypes.c_int),
+        "cdbm_macros": ([ctx, _vp, _vp, _vp, _vp], ctypes.c_int),
+        "cdbm_tne": ([ctx, _vp], ctypes.c_int),
+        "cdbm_conserved_sums": ([ctx, _dp], ctypes.c_int),
+        "cdbm_get_state": ([ctx, _vp, _dp], ctypes.c_int),
+        "cdbm_set_state": ([ctx, _vp, ctypes.c_double], ctypes.c_int),
+        "cdbm_state_ptr": ([ctx, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+        "cdbm_time": ([ctx, _dp], ctypes.c_int),
+        "cdbm_sync": ([ctx], ctypes.c_int),
+        "cdbm_last_error": ([ctx], ctypes.c_char_p),
+        "cdbm_destroy": ([ctx], None),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(lib, ctx, status):
+    if status != CDBM_OK:
+        raise CdbmError(status, lib.cdbm_last_error(ctx).decode())
+
+
+# ---- thin wrappers with the C names (pointers are ints / ctypes values) ----
+
+def cdbm_create(grid: cdbm_grid, vset: cdbm_vset, I, tau, dt, precision=CDBM_FP64, stream=0,
+                allocator: cdbm_allocator | None = None):
+    lib = load()
+    out = ctypes.c_void_p()
+    st = lib.cdbm_create(ctypes.byref(grid), ctypes.byref(vset), float(I), float(tau), float(dt),
+                         int(precision), ctypes.c_void_p(stream),
+                         ctypes.byref(allocator) if allocator is not None else None, ctypes.byref(out))
+    _check(lib, None, st)
+    return out
+
+
+def cdbm_set_rk(ctx, rk):
+    lib = load()
+    _check(lib, ctx, lib.cdbm_set_rk(ctx, int(rk)))
+
+
+def cdbm_init(ctx, rho, ux, uy, T):
+    lib = load()
+    _check(lib, ctx, lib.cdbm_init(ctx, rho, ux, uy, T))
+
+
+def cdbm_step(ctx, nsteps):
+    lib = load()
+    _check(lib, ctx, lib.cdbm_step(ctx, int(nsteps)))
+
+
+def cdbm_macros(ctx, rho, ux, uy, T):
+    lib = load()
+    _check(lib, ctx, lib.cdbm_macros(ctx, rho, ux, uy, T))
+
+
+def cdbm_tne(ctx, out):
+    lib = load()
+    _check(lib, ctx, lib.cdbm_tne(ctx, out))
+
+
+def cdbm_conserved_sums(ctx):
+    lib = load()
+    out = (ctypes.c_double * 4)()
+    _check(lib, ctx, lib.cdbm_conserved_sums(ctx, out))
+    return np.array(out[:])
+
+
+def cdbm_get_state(ctx, f):
+    lib = load()
+    t = ctypes.c_double()
+    _check(lib, ctx, lib.cdbm_get_state(ctx, f, ctypes.byref(t)))
+    return t.value
+
+
+def cdbm_set_state(ctx, f, t):
+    lib = load()
+    _check(lib, ctx, lib.cdbm_set_state(ctx, f, float(t)))
+
+
+def cdbm_state_ptr(ctx) -> int:
+    lib = load()
+    p = ctypes.c_void_p()
+    _check(lib, ctx, lib.cdbm_state_ptr(ctx, ctypes.byref(p)))
+    return p.value
+
+
+def cdbm_time(ctx) -> float:
+    lib = load()
+    t = ctypes.c_double()
+    _check(lib, ctx, lib.cdbm_time(ctx, ctypes.byref(t)))
+    return t.value
+
+
+def cdbm_sync(ctx):
+    lib = load()
+    _check(lib, ctx, lib.cdbm_sync(ctx))
+
+
+def cdbm_last_error(ctx) -> str:
+    return load().cdbm_last_error(ctx).decode()
+
+
+def cdbm_destroy(ctx):
+    load().cdbm_destroy(ctx)
+
+
+# ------------------------------------------------------------------ Solver
+
+def _ptr(x):
+    """Device or host address of a torch tensor / numpy array (float64, contiguous)."""
+    if isinstance(x, np.ndarray):
+        assert x.dtype == np.float64 and x.flags["C_CONTIGUOUS"], "need contiguous float64"
+        return x.ctypes.data
+    assert x.dtype.is_floating_point and x.element_size() == 8 and x.is_contiguous(), \
+        "need a contiguous float64 tensor"
+    return x.data_ptr()
+
+
+class Solver:
+    """One CDBM run on the current CUDA device.
+
+    Parameters follow ``cdbm_create``: grid size and spacing, boundary kinds,
+    relaxation time ``tau``, time step ``dt``, extra degrees of freedom ``I`` and
+    the velocity set ``vg`` = (v_a..v_d), ``eg`` = (eta_a..eta_d) of Eqs. (2)-(3).
+    Work runs on ``stream`` (a torch.cuda.Stream; default: the current stream).
+    """
+
+    def __init__(self, nx, ny, dx, dy, dt, tau, I, vg, eg, bc_x=CDBM_BC_PERIODIC,
+                 bc_y=CDBM_BC_PERIODIC, precision=CDBM_FP64, rk=CDBM_RK2_TVD, stream=None):
+        import torch
+        self._torch = torch
+        self.nx, self.ny = int(nx), int(ny)
+        self.device = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        dev = self.device
+
+        def _alloc(nbytes, strm, user):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev, strm or 0)
+            except Exception:      # reported to the library as NULL -> CDBM_ENOMEM
+                return None
+
+        def _free(ptr, nbytes, strm, user):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._alloc_cb = ALLOC_FN(_alloc)
+        self._free_cb = FREE_FN(_free)
+        self._allocator = cdbm_allocator(self._alloc_cb, self._free_cb, None)
+        grid = cdbm_grid(self.nx, self.ny, float(dx), float(dy), int(bc_x), int(bc_y))
+        vset = cdbm_vset((ctypes.c_double * 4)(*vg), (ctypes.c_double * 4)(*eg))
+        self.ctx = cdbm_create(grid, vset, I, tau, dt, precision, self.stream.cuda_stream,
+                               self._allocator)
+        if rk != CDBM_RK2_TVD:
+            cdbm_set_rk(self.ctx, rk)
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        return cls(w.nx, w.ny, w.dx, w.dy, w.dt, w.tau, w.I, w.vg, w.eg, w.bc_x, w.bc_y, **kw)
+
+    # -- fields -------------------------------------------------------------
+    def _field(self, a):
+        torch = self._torch
+        if isinstance(a, np.ndarray) or not hasattr(a, "data_ptr"):
+            a = np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64),
+                                                     (self.ny, self.nx)))
+            return a, a.ctypes.data
+        a = a.to(torch.float64).contiguous()
+        return a, a.data_ptr()
+
+    def init(self, rho, ux, uy, T):
+        keep = [self._field(a) for a in (rho, ux, uy, T)]
+        cdbm_init(self.ctx, *(p for _, p in keep))
+        for a, _ in keep:
+            if hasattr(a, "record_stream"):
+                a.record_stream(self.stream)
+
+    def step(self, nsteps=1):
+        cdbm_step(self.ctx, nsteps)
+
+    def macros(self):
+        """(rho, ux, uy, T) as new [ny][nx] float64 CUDA tensors."""
+        torch = self._torch
+        out = [torch.empty((self.ny, self.nx), dtype=torch.float64, device=self.device)
+               for _ in range(4)]
+        cdbm_macros(self.ctx, *(t.data_ptr() for t in out))
+        return tuple(out)
+
+    def tne(self):
+        torch = self._torch
+        out = torch.empty((12, self.ny, self.nx), dtype=torch.float64, device=self.device)
+        cdbm_tne(self.ctx, out.data_ptr())
+        return out
+
+    def conserved_sums(self):
+        return cdbm_conserved_sums(self.ctx)
+
+    def state(self):
+        torch = self._torch
+        out = torch.empty((16, self.ny, self.nx), dtype=torch.float64, device=self.device)
+        cdbm_get_state(self.ctx, out.data_ptr())
+        return out
+
+    def set_state(self, f, t=0.0):
+        a, p = (f, _ptr(f)) if isinstance(f, np.ndarray) else (f.contiguous(), None)
+        cdbm_set_state(self.ctx, p if p is not None else a.data_ptr(), t)
+
+    @property
+    def time(self):
+        return cdbm_time(self.ctx)
+
+    def sync(self):
+        cdbm_sync(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            cdbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,645 @@
+// Host side of the CDBM library: the C ABI of include/cdbm.h, validation, the
+// parity-blocked inverse moment matrix, buffers and the CUDA graph of time steps.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/cdbm.h"
+#include "cdbm_device.cuh"
+#include "cdbm_internal.h"
+
+using namespace cdbm;
+
+namespace {
+
+thread_local char g_create_error[256] = "no error";
+
+constexpr int kGraphSteps = 32;       // time steps per replayed CUDA graph
+constexpr double kMaxCond = 1e12;     // condition limit of the moment blocks
+
+struct RkStage {
+    double alpha, beta, gamma;        // out = alpha f^n + beta g + gamma dt L(g)
+    bool with_base;
+};
+
+void rk_stages(int rk, RkStage st[2])
+{
+    if (rk == CDBM_RK2_MIDPOINT) {
+        st[0] = {0.0, 1.0, 0.5, false};
+        st[1] = {1.0, 0.0, 1.0, true};
+    } else {
+        st[0] = {0.0, 1.0, 1.0, false};
+        st[1] = {0.5, 0.5, 0.5, true};
+    }
+}
+
+}  // namespace
+
+struct cdbm_ctx {
+    cdbm_grid grid;
+    cdbm_vset vset;
+    double I, tau, dt;
+    int precision;
+    int rk;
+    cudaStream_t stream;
+    cdbm_allocator alloc;
+    bool user_alloc;
+    int device;
+    int sm_count;
+
+    size_t plane;                 // nx * ny
+    double *f;                    // state [16][ny][nx]
+    double *f1;                   // stage buffer [16][ny][nx]; also staging for host I/O
+    double *partials;             // conserved-sum partials [nblocks][4]
+    double *sums;                 // 4 doubles
+    unsigned *flag;               // device error flags
+    unsigned *flag_host;          // pinned mirror
+    int sum_blocks;
+    bool state_set;
+    double t;
+
+    EqBlocks eq_unit;
+    ModelConsts mc;
+    StageArgs stage[2];
+    StageLaunch launch[2];
+    RkStage rks[2];
+    FieldArgs fields;
+
+    cudaGraphExec_t graph;
+
+    cdbm_status err;
+    char msg[256];
+};
+
+namespace {
+
+cdbm_status set_err(cdbm_ctx *c, cdbm_status s, const char *fmt, ...)
+{
+    if (c->err != CDBM_OK) return c->err;
+    c->err = s;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->msg, sizeof(c->msg), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+cdbm_status create_err(cdbm_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_create_error, sizeof(g_create_error), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+cdbm_status cuda_check(cdbm_ctx *c, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return CDBM_OK;
+    return set_err(c, CDBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void *ctx_alloc(cdbm_ctx *c, size_t bytes)
+{
+    if (c->user_alloc) return c->alloc.alloc(bytes, (void *)c->stream, c->alloc.user);
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void ctx_free(cdbm_ctx *c, void *p, size_t bytes)
+{
+    if (!p) return;
+    if (c->user_alloc)
+        c->alloc.free(p, bytes, (void *)c->stream, c->alloc.user);
+    else
+        cudaFreeAsync(p, c->stream);
+}
+
+bool is_device_pointer(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// In-place Gauss-Jordan inverse with partial pivoting; cond = ||A||_inf ||A^-1||_inf.
+bool invert(int n, const double *A, double *Ainv, double *cond)
+{
+    double a[4][8];
+    double anorm = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double rs = 0.0;
+        for (int j = 0; j < n; ++j) {
+            a[i][j] = A[i * n + j];
+            a[i][n + j] = (i == j) ? 1.0 : 0.0;
+            rs += std::fabs(A[i * n + j]);
+        }
+        anorm = rs > anorm ? rs : anorm;
+    }
+    for (int k = 0; k < n; ++k) {
+        int p = k;
+        for (int i = k + 1; i < n; ++i)
+            if (std::fabs(a[i][k]) > std::fabs(a[p][k])) p = i;
+        if (a[p][k] == 0.0 || !std::isfinite(a[p][k])) return false;
+        if (p != k)
+            for (int j = 0; j < 2 * n; ++j) std::swap(a[k][j], a[p][j]);
+        const double piv = a[k][k];
+        for (int j = 0; j < 2 * n; ++j) a[k][j] /= piv;
+        for (int i = 0; i < n; ++i) {
+            if (i == k) continue;
+            const double m = a[i][k];
+            if (m == 0.0) continue;
+            for (int j = 0; j < 2 * n; ++j) a[i][j] -= m * a[k][j];
+        }
+    }
+    double inorm = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double rs = 0.0;
+        for (int j = 0; j < n; ++j) {
+            Ainv[i * n + j] = a[i][n + j];
+            rs += std::fabs(a[i][n + j]);
+        }
+        inorm = rs > inorm ? rs : inorm;
+    }
+    *cond = anorm * inorm;
+    return std::isfinite(*cond);
+}
+
+// Model constants and the unscaled parity-blocked inverse of M(0) (Eq. 6 at u = 0),
+// with the factors 1/4 (s0, dq, q; diagonal sx, sy) and 1/2 (axis sx, sy) that
+// rebuild f_i from group components folded into the rows.
+cdbm_status build_blocks(const cdbm_vset &vs, double I, ModelConsts &m, EqBlocks &eq, double *cond_out,
+                         const char **which)
+{
+    const double K = 2.0 + I;
+    double vv[4];
+    for (int g = 0; g < 4; ++g) {
+        const double c = vs.v[g];
+        m.c[g] = c;
+        vv[g] = (g & 1) ? 2.0 * c * c : c * c;
+        m.w[g] = vv[g] + vs.eta[g] * vs.eta[g];
+    }
+    m.K = K;
+    m.invK = 1.0 / K;
+    m.Kp2 = K + 2.0;
+    m.Kp4 = K + 4.0;
+    m.Kp6 = K + 6.0;
+    m.twoKp2 = 2.0 * (K + 2.0);
+
+    double AS[16], AB1[4], AB2[4], AV[16];
+    for (int g = 0; g < 4; ++g) {
+        const double c = m.c[g];
+        AS[0 * 4 + g] = 1.0;
+        AS[1 * 4 + g] = m.w[g];
+        AS[2 * 4 + g] = vv[g];
+        AS[3 * 4 + g] = m.w[g] * vv[g];
+        AV[0 * 4 + g] = c;
+        AV[1 * 4 + g] = m.w[g] * c;
+        AV[2 * 4 + g] = c * c * c;
+        AV[3 * 4 + g] = (g & 1) ? c * c * c : 0.0;
+    }
+    const double ca = m.c[0], cc = m.c[2], cb = m.c[1], cd = m.c[3];
+    AB1[0] = ca * ca;
+    AB1[1] = cc * cc;
+    AB1[2] = m.w[0] * ca * ca;
+    AB1[3] = m.w[2] * cc * cc;
+    AB2[0] = cb * cb;
+    AB2[1] = cd * cd;
+    AB2[2] = m.w[1] * cb * cb;
+    AB2[3] = m.w[3] * cd * cd;
+
+    double cond[4];
+    double SI[16], B1I[4], B2I[4], VI[16];
+    const char *names[4] = {"scalar", "axis quadrupole", "diagonal quadrupole", "vector"};
+    bool ok[4] = {invert(4, AS, SI, &cond[0]), invert(2, AB1, B1I, &cond[1]),
+                  invert(2, AB2, B2I, &cond[2]), invert(4, AV, VI, &cond[3])};
+    double worst = 0.0;
+    for (int b = 0; b < 4; ++b) {
+        if (!ok[b] || cond[b] > kMaxCond) {
+            *which = names[b];
+            *cond_out = ok[b] ? cond[b] : INFINITY;
+            return CDBM_ESINGULAR;
+        }
+        worst = cond[b] > worst ? cond[b] : worst;
+    }
+    *cond_out = worst;
+    for (int g = 0; g < 4; ++g) {
+        const double fv = (g & 1) ? 0.25 : 0.5;
+        for (int k = 0; k < 4; ++k) {
+            eq.S[g * 4 + k] = 0.25 * SI[g * 4 + k];
+            eq.V[g * 4 + k] = fv * VI[g * 4 + k];
+        }
+    }
+    for (int k = 0; k < 4; ++k) {
+        eq.B1[k] = 0.25 * B1I[k];
+        eq.B2[k] = 0.25 * B2I[k];
+    }
+    return CDBM_OK;
+}
+
+EqBlocks scaled(const EqBlocks &e, double s)
+{
+    EqBlocks o;
+    for (int k = 0; k < 16; ++k) {
+        o.S[k] = s * e.S[k];
+        o.V[k] = s * e.V[k];
+    }
+    for (int k = 0; k < 4; ++k) {
+        o.B1[k] = s * e.B1[k];
+        o.B2[k] = s * e.B2[k];
+    }
+    return o;
+}
+
+void build_stages(cdbm_ctx *c)
+{
+    rk_stages(c->rk, c->rks);
+    const double h = c->dt / c->tau;
+    for (int s = 0; s < 2; ++s) {
+        const RkStage &r = c->rks[s];
+        StageArgs &a = c->stage[s];
+        a.eq = scaled(c->eq_unit, r.gamma * h);
+        a.m = c->mc;
+        a.a_base = r.alpha;
+        a.a_self = r.beta - r.gamma * h;
+        for (int g = 0; g < 4; ++g) {
+            a.lx[g] = r.gamma * c->dt * c->mc.c[g] / c->grid.dx;
+            a.ly[g] = r.gamma * c->dt * c->mc.c[g] / c->grid.dy;
+        }
+        a.nx = c->grid.nx;
+        a.ny = c->grid.ny;
+        a.bc_x = c->grid.bc_x;
+        a.bc_y = c->grid.bc_y;
+        c->launch[s] = stage_launch_config(a, r.with_base, c->sm_count);
+    }
+}
+
+cdbm_status enqueue_step(cdbm_ctx *c)
+{
+    cudaError_t e = launch_stage(c->launch[0], c->f, nullptr, c->f1, c->stage[0], c->flag, c->stream);
+    if (e == cudaSuccess)
+        e = launch_stage(c->launch[1], c->f1, c->f, c->f, c->stage[1], c->flag, c->stream);
+    return cuda_check(c, e, "stage launch");
+}
+
+// Explicitly built graph of kGraphSteps steps (two kernel nodes per step); no
+// stream capture, so it works on the legacy default stream too.
+cdbm_status build_graph(cdbm_ctx *c)
+{
+    cudaGraph_t g;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) return cuda_check(c, cudaGetLastError(), "graph create");
+    cudaGraphNode_t prev = nullptr;
+    const double *nil = nullptr;
+    for (int s = 0; s < kGraphSteps; ++s) {
+        for (int k = 0; k < 2; ++k) {
+            const double *gin = (k == 0) ? c->f : c->f1;
+            const double *base = (k == 0) ? nil : c->f;
+            double *out = (k == 0) ? c->f1 : c->f;
+            void *args[] = {(void *)&gin, (void *)&base, (void *)&out, (void *)&c->stage[k],
+                            (void *)&c->flag};
+            cudaKernelNodeParams p;
+            memset(&p, 0, sizeof(p));
+            p.func = c->launch[k].func;
+            p.gridDim = c->launch[k].grid;
+            p.blockDim = c->launch[k].block;
+            p.sharedMemBytes = 0;
+            p.kernelParams = args;
+            cudaGraphNode_t node;
+            cudaError_t e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &p);
+            if (e != cudaSuccess) {
+                cudaGraphDestroy(g);
+                return cuda_check(c, e, "graph add node");
+            }
+            prev = node;
+        }
+    }
+    cudaError_t e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->graph = nullptr;
+        return cuda_check(c, e, "graph instantiate");
+    }
+    return CDBM_OK;
+}
+
+void drop_graph(cdbm_ctx *c)
+{
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+}  // namespace
+
+extern "C" {
+
+cdbm_status cdbm_create(const cdbm_grid *grid, const cdbm_vset *vset, double I, double tau, double dt,
+                        int precision, void *cuda_stream, const cdbm_allocator *allocator,
+                        cdbm_ctx **out)
+{
+    if (!out) return create_err(CDBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!grid || !vset) return create_err(CDBM_EINVAL, "grid or vset is NULL");
+    if (grid->nx < 1 || grid->ny < 1)
+        return create_err(CDBM_EINVAL, "grid %d x %d: both sizes must be >= 1", grid->nx, grid->ny);
+    if (!finite_pos(grid->dx) || !finite_pos(grid->dy) || !finite_pos(dt) || !finite_pos(tau))
+        return create_err(CDBM_EINVAL, "dx, dy, dt and tau must be finite and > 0");
+    if (!(std::isfinite(I) && I >= 0.0)) return create_err(CDBM_EINVAL, "I must be finite and >= 0");
+    if ((grid->bc_x != 0 && grid->bc_x != 1) || (grid->bc_y != 0 && grid->bc_y != 1))
+        return create_err(CDBM_EINVAL, "unknown boundary kind");
+    if (precision != CDBM_FP64) return create_err(CDBM_EINVAL, "unsupported precision %d", precision);
+    for (int g = 0; g < 4; ++g)
+        if (!std::isfinite(vset->v[g]) || !std::isfinite(vset->eta[g]) || vset->v[g] <= 0.0 ||
+            vset->eta[g] < 0.0)
+            return create_err(CDBM_EINVAL, "velocity set: v must be > 0 and eta >= 0");
+    if (dt / tau > 2.0)
+        return create_err(CDBM_EINVAL, "dt/tau = %g exceeds 2 (RK2 relaxation stability)", dt / tau);
+    double cfl = 0.0;
+    for (int i = 0; i < kNV; ++i) {
+        const double s = vset->v[i >> 2];
+        const double cx = grid->nx > 1 ? std::abs(dirx(i)) * s * dt / grid->dx : 0.0;
+        const double cy = grid->ny > 1 ? std::abs(diry(i)) * s * dt / grid->dy : 0.0;
+        cfl = cx + cy > cfl ? cx + cy : cfl;
+    }
+    if (cfl > 1.0) return create_err(CDBM_EINVAL, "CFL number %g exceeds 1", cfl);
+    if ((size_t)grid->nx * grid->ny > ((size_t)1 << 40))
+        return create_err(CDBM_EINVAL, "grid too large");
+
+    cdbm_ctx *c = new (std::nothrow) cdbm_ctx();
+    if (!c) return create_err(CDBM_ENOMEM, "host allocation failed");
+    c->grid = *grid;
+    c->vset = *vset;
+    c->I = I;
+    c->tau = tau;
+    c->dt = dt;
+    c->precision = precision;
+    c->rk = CDBM_RK2_TVD;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->user_alloc = allocator && allocator->alloc && allocator->free;
+    if (c->user_alloc) c->alloc = *allocator;
+    c->err = CDBM_OK;
+    strcpy(c->msg, "no error");
+    c->plane = (size_t)grid->nx * grid->ny;
+
+    double cond = 0.0;
+    const char *which = "";
+    if (build_blocks(*vset, I, c->mc, c->eq_unit, &cond, &which) != CDBM_OK) {
+        delete c;
+        return create_err(CDBM_ESINGULAR, "moment matrix block '%s' singular (cond %g)", which, cond);
+    }
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        cudaError_t e = cudaGetLastError();
+        delete c;
+        return create_err(CDBM_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    }
+    c->sum_blocks = 2 * c->sm_count;
+    build_stages(c);
+    c->fields.eq = c->eq_unit;
+    c->fields.m = c->mc;
+    for (int i = 0; i < kNV; ++i) {
+        const double s = vset->v[i >> 2];
+        c->fields.vx[i] = dirx(i) * s;
+        c->fields.vy[i] = diry(i) * s;
+        c->fields.eta[i] = vset->eta[i >> 2];
+    }
+    c->fields.nx = grid->nx;
+    c->fields.ny = grid->ny;
+
+    const size_t fbytes = sizeof(double) * kNV * c->plane;
+    c->f = (double *)ctx_alloc(c, fbytes);
+    c->f1 = (double *)ctx_alloc(c, fbytes);
+    c->partials = (double *)ctx_alloc(c, sizeof(double) * 4 * c->sum_blocks + sizeof(double) * 4 + 256);
+    if (!c->f || !c->f1 || !c->partials || cudaMallocHost(&c->flag_host, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        ctx_free(c, c->f, fbytes);
+        ctx_free(c, c->f1, fbytes);
+        ctx_free(c, c->partials, 0);
+        cudaStreamSynchronize(c->stream);
+        delete c;
+        return create_err(CDBM_ENOMEM, "device allocation of %zu bytes failed", 2 * fbytes);
+    }
+    c->sums = c->partials + 4 * c->sum_blocks;
+    c->flag = (unsigned *)(c->sums + 4);
+    *c->flag_host = 0;
+    if (cudaMemsetAsync(c->flag, 0, sizeof(unsigned), c->stream) != cudaSuccess) {
+        cudaError_t e = cudaGetLastError();
+        cdbm_destroy(c);
+        return create_err(CDBM_ECUDA, "memset: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return CDBM_OK;
+}
+
+cdbm_status cdbm_set_rk(cdbm_ctx *c, int rk)
+{
+    if (!c) return CDBM_EINVAL;
+    if (c->err) return c->err;
+    if (rk != CDBM_RK2_TVD && rk != CDBM_RK2_MIDPOINT) return CDBM_EINVAL;
+    if (rk != c->rk) {
+        c->rk = rk;
+        drop_graph(c);
+        build_stages(c);
+    }
+    return CDBM_OK;
+}
+
+cdbm_status cdbm_init(cdbm_ctx *c, const double *rho, const double *ux, const double *uy,
+                      const double *T)
+{
+    if (!c) return CDBM_EINVAL;
+    if (c->err) return c->err;
+    if (!rho || !ux || !uy || !T) return set_err(c, CDBM_EINVAL, "cdbm_init: NULL field");
+    const double *src[4] = {rho, ux, uy, T};
+    const double *dev[4];
+    bool any_host = false;
+    const size_t bytes = sizeof(double) * c->plane;
+    for (int k = 0; k < 4; ++k) {
+        if (is_device_pointer(src[k])) {
+            dev[k] = src[k];
+        } else {
+            any_host = true;
+            double *dst = c->f1 + k * c->plane;
+            if (cuda_check(c, cudaMemcpyAsync(dst, src[k], bytes, cudaMemcpyHostToDevice, c->stream),
+                           "cdbm_init upload"))
+                return c->err;
+            dev[k] = dst;
+        }
+    }
+    if (cuda_check(c, launch_init(c->fields, dev[0], dev[1], dev[2], dev[3], c->f, c->flag, c->stream),
+                   "init launch"))
+        return c->err;
+    if (any_host && cuda_check(c, cudaStreamSynchronize(c->stream), "cdbm_init sync")) return c->err;
+    c->t = 0.0;
+    c->state_set = true;
+    return CDBM_OK;
+}
+
+cdbm_status cdbm_step(cdbm_ctx *c, int nsteps)
+{
+    if (!c) return CDBM_EINVAL;
+    if (c->err) return c->err;
+    if (nsteps < 0) return set_err(c, CDBM_EINVAL, "cdbm_step: nsteps < 0");
+    if (!c->state_set) return set_err(c, CDBM_EINVAL, "cdbm_step: state not initialised");
+    int left = nsteps;
+    if (left >= kGraphSteps && !c->graph && build_graph(c)) return c->err;
+    while (left >= kGraphSteps) {
+        if (cuda_check(c, cudaGraphLaunch(c->graph, c->stream), "graph launch")) return c->err;
+        left -= kGraphSteps;
+    }
+    for (; left > 0; --left)
+        if (enqueue_step(c)) return c->err;
+    c->t += nsteps * c->dt;
+    return CDBM_OK;
+}
+
+cdbm_status cdbm_macros(cdbm_ctx *c, double *rho, double *ux, double *uy, double *T)
+{
+    if (!c) return CDBM_EINVAL;
+    if (c->err) return c->err;
+    if (!c->state_set) return set_err(c, CDBM_EINVAL, "cdbm_macros: state not initialised");
+    double *dst[4] = {rho, ux, uy, T};
+    double *dev[4];
+    bool host[4];
+    bool any_host = false;
+    for (int k = 0; k < 4; ++k) {
+        host[k] = dst[k] && !is_device_pointer(dst[k]);
+        any_host |= host[k];
+        dev[k] = host[k] ? c->f1 + k * c->plane : dst[k];
+    }
+    if (cuda_check(c, launch_macros(c->fields, c->f, dev[0], dev[1], dev[2], dev[3], c->stream),
+                   "macros launch"))
+        return c->err;
+    for (int k = 0; k < 4; ++k)
+        if (host[k] && cuda_check(c, cudaMemcpyAsync(dst[k], dev[k], sizeof(double) * c->plane,
+                                                     cudaMemcpyDeviceToHost, c->stream),
+                                  "cdbm_macros download"))
+            return c->err;
+    if (any_host && cuda_check(c, cudaStreamSynchronize(c->stream), "cdbm_macros sync")) return c->err;
+    return CDBM_OK;
+}
+
+cdbm_status cdbm_tne(cdbm_ctx *c, double *out)
+{
+    if (!c) return CDBM_EINVAL;
+    if (c->err) return c->err;
+    if (!out) return set_err(c, CDBM_EINVAL, "cdbm_tne: NULL output");
+    if (!c->state_set) return set_err(c, CDBM_EINVAL, "cdbm_tne: state not initialised");
+    const bool host = !is_device_pointer(out);
+    double *dev = host ? c->f1 : out;
+    if (cuda_check(c, launch_tne(c->fields, c->f, dev, c->stream), "tne launch")) return c->err;
+    if (host) {
+        if (cuda_check(c, cudaMemcpyAsync(out, dev, sizeof(double) * 12 * c->plane,
+                                          cudaMemcpyDeviceToHost, c->stream), "cdbm_tne download") ||
+            cuda_check(c, cudaStreamSynchronize(c->stream), "cdbm_tne sync"))
+            return c->err;
+    }
+    return CDBM_OK;
+}
+
+cdbm_status cdbm_conserved_sums(cdbm_ctx *c, double out[4])
+{
+    if (!c) return CDBM_EINVAL;
+    if (c->err) return c->err;
+    if (!out) return set_err(c, CDBM_EINVAL, "cdbm_conserved_sums: NULL output");
+    if (!c->state_set) return set_err(c, CDBM_EINVAL, "cdbm_conserved_sums: state not initialised");
+    if (cuda_check(c, launch_sums(c->fields, c->f, c->partials, c->sum_blocks, c->sums, c->stream),
+                   "sums launch") ||
+        cuda_check(c, cudaMemcpyAsync(out, c->sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                   "sums download") ||
+        cuda_check(c, cudaStreamSynchronize(c->stream), "sums sync"))
+        return c->err;
+    return CDBM_OK;
+}
+
+cdbm_status cdbm_get_state(cdbm_ctx *c, double *f, double *t)
+{
+    if (!c) return CDBM_EINVAL;
+    if (c->err) return c->err;
+    if (f) {
+        if (!c->state_set) return set_err(c, CDBM_EINVAL, "cdbm_get_state: state not initialised");
+        const bool host = !is_device_pointer(f);
+        if (cuda_check(c, cudaMemcpyAsync(f, c->f, sizeof(double) * kNV * c->plane, cudaMemcpyDefault,
+                                          c->stream), "cdbm_get_state copy"))
+            return c->err;
+        if (host && cuda_check(c, cudaStreamSynchronize(c->stream), "cdbm_get_state sync")) return c->err;
+    }
+    if (t) *t = c->t;
+    return CDBM_OK;
+}
+
+cdbm_status cdbm_set_state(cdbm_ctx *c, const double *f, double t)
+{
+    if (!c) return CDBM_EINVAL;
+    if (c->err) return c->err;
+    if (!f || !std::isfinite(t)) return set_err(c, CDBM_EINVAL, "cdbm_set_state: bad argument");
+    const bool host = !is_device_pointer(f);
+    if (cuda_check(c, cudaMemcpyAsync(c->f, f, sizeof(double) * kNV * c->plane, cudaMemcpyDefault,
+                                      c->stream), "cdbm_set_state copy"))
+        return c->err;
+    if (host && cuda_check(c, cudaStreamSynchronize(c->stream), "cdbm_set_state sync")) return c->err;
+    c->t = t;
+    c->state_set = true;
+    return CDBM_OK;
+}
+
+cdbm_status cdbm_state_ptr(cdbm_ctx *c, double **f)
+{
+    if (!c || !f) return CDBM_EINVAL;
+    *f = c->f;
+    return c->err;
+}
+
+cdbm_status cdbm_time(const cdbm_ctx *c, double *t)
+{
+    if (!c || !t) return CDBM_EINVAL;
+    *t = c->t;
+    return c->err;
+}
+
+cdbm_status cdbm_sync(cdbm_ctx *c)
+{
+    if (!c) return CDBM_EINVAL;
+    if (c->err) return c->err;
+    if (cuda_check(c, cudaMemcpyAsync(c->flag_host, c->flag, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                      c->stream), "flag download") ||
+        cuda_check(c, cudaStreamSynchronize(c->stream), "cdbm_sync"))
+        return c->err;
+    if (*c->flag_host & kFlagNonPhys)
+        return set_err(c, CDBM_ENONPHYS, "non-physical state (rho <= 0, T <= 0 or non-finite) at t = %g",
+                       c->t);
+    return CDBM_OK;
+}
+
+const char *cdbm_last_error(const cdbm_ctx *c)
+{
+    return c ? c->msg : g_create_error;
+}
+
+void cdbm_destroy(cdbm_ctx *c)
+{
+    if (!c) return;
+    drop_graph(c);
+    const size_t fbytes = sizeof(double) * kNV * c->plane;
+    ctx_free(c, c->f, fbytes);
+    ctx_free(c, c->f1, fbytes);
+    ctx_free(c, c->partials, sizeof(double) * 4 * c->sum_blocks + sizeof(double) * 4 + 256);
+    cudaStreamSynchronize(c->stream);
+    if (c->flag_host) cudaFreeHost(c->flag_host);
+    cudaGetLastError();
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,174 @@
+// Device building blocks of the CDBM kernels: velocity-set geometry, the
+// conserved moments, the factored equilibrium, the minmod limiter and the NND
+// transport difference.  Everything here is double precision; integer work
+// (limiter decisions, validity tests, neighbour indices) is kept off the FP64
+// pipe, which is the scarce unit on GB300.
+#pragma once
+
+#include <cstdint>
+
+#include "cdbm_internal.h"
+
+namespace cdbm {
+
+// Direction signs of velocity i (Eq. 2 with the fixed member order: axis groups
+// (1,0),(0,1),(-1,0),(0,-1); diagonal groups (1,1),(-1,1),(-1,-1),(1,-1)).
+__host__ __device__ constexpr int dirx(int i)
+{
+    return ((i >> 2) & 1) == 0 ? ((i & 3) == 0 ? 1 : ((i & 3) == 2 ? -1 : 0))
+                               : (((i & 3) == 0 || (i & 3) == 3) ? 1 : -1);
+}
+__host__ __device__ constexpr int diry(int i)
+{
+    return ((i >> 2) & 1) == 0 ? ((i & 3) == 1 ? 1 : ((i & 3) == 3 ? -1 : 0))
+                               : (((i & 3) <= 1) ? 1 : -1);
+}
+
+// true iff v > 0 and v is finite (sign, zero and exponent tested on the bits).
+__device__ __forceinline__ bool positive_finite(double v)
+{
+    const long long b = __double_as_longlong(v);
+    return b > 0 && b < 0x7ff0000000000000LL;
+}
+
+// minmod of Eq. (16) on the integer pipe: zero when either argument is zero or
+// the signs differ, otherwise the argument of smaller magnitude (X on a tie).
+// Magnitudes of finite doubles order like their bit patterns without the sign.
+__device__ __forceinline__ double minmod(double X, double Y)
+{
+    const long long x = __double_as_longlong(X);
+    const long long y = __double_as_longlong(Y);
+    const long long ax = x & 0x7fffffffffffffffLL;
+    const long long ay = y & 0x7fffffffffffffffLL;
+    const long long pick = (ax <= ay) ? x : y;
+    const bool keep = ((x ^ y) >= 0) & (ax != 0) & (ay != 0);
+    return __longlong_as_double(keep ? pick : 0LL);
+}
+
+// NND transport difference (Eqs. 12-20) in upwind order.  For a velocity
+// component v along r, with u2, u1 the values two and one cells upwind, c the
+// cell and d1 one cell downwind,
+//   (H(j+1/2) - H(j-1/2)) / |v| = (c - u1) + [minmod(d1 - c, c - u1) - minmod(c - u1, u1 - u2)] / 2,
+// which is Eqs. (13)-(20) for v > 0 and their mirror image for v < 0
+// (f+ = v f, f- = 0, resp. f+ = 0, f- = v f).
+__device__ __forceinline__ double nnd(double u2, double u1, double c, double d1)
+{
+    const double a = c - u1;
+    const double b = d1 - c;
+    const double e = u1 - u2;
+    const double t = minmod(b, a) - minmod(a, e);
+    return fma(0.5, t, a);
+}
+
+// 1 / a for a > 0: hardware estimate refined by one cubic Newton-Raphson step,
+// r (1 + e + e^2) with e = 1 - a r (error ~ e^3, below one ulp).
+__device__ __forceinline__ double rcp64(double a)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(a));
+    const double e = fma(-a, r, 1.0);
+    return fma(r, fma(e, e, e), r);
+}
+
+struct Cons {
+    double rho, jx, jy, E;   // sum f, sum f v_x, sum f v_y, sum f (v^2 + eta^2)
+};
+
+// Conserved moments of f (Eq. 4 rows 1-4 with f in place of f_eq), accumulated
+// through the group components s0, sx, sy.
+__device__ __forceinline__ Cons conserved(const double f[kNV], const ModelConsts &m)
+{
+    double s0[4], sx[4], sy[4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const double *q = f + 4 * g;
+        if ((g & 1) == 0) {          // axis: E N W S
+            sx[g] = q[0] - q[2];
+            sy[g] = q[1] - q[3];
+            s0[g] = (q[0] + q[2]) + (q[1] + q[3]);
+        } else {                     // diagonal: NE NW SW SE
+            const double e = q[0] + q[3], w = q[1] + q[2];
+            sx[g] = e - w;
+            sy[g] = (q[0] + q[1]) - (q[2] + q[3]);
+            s0[g] = e + w;
+        }
+    }
+    Cons r;
+    r.rho = (s0[0] + s0[1]) + (s0[2] + s0[3]);
+    r.jx = fma(m.c[3], sx[3], fma(m.c[2], sx[2], fma(m.c[1], sx[1], m.c[0] * sx[0])));
+    r.jy = fma(m.c[3], sy[3], fma(m.c[2], sy[2], fma(m.c[1], sy[1], m.c[0] * sy[0])));
+    r.E = fma(m.w[3], s0[3], fma(m.w[2], s0[2], fma(m.w[1], s0[1], m.w[0] * s0[0])));
+    return r;
+}
+
+__device__ __forceinline__ void rebuild_axis(double *o, double s0, double dq, double sx, double sy)
+{
+    const double A = s0 + dq, B = s0 - dq;
+    o[0] = A + sx;
+    o[2] = A - sx;
+    o[1] = B + sy;
+    o[3] = B - sy;
+}
+
+__device__ __forceinline__ void rebuild_diag(double *o, double s0, double q, double sx, double sy)
+{
+    const double P = s0 + q, Q = s0 - q, U = sx + sy, V = sx - sy;
+    o[0] = P + U;   // NE
+    o[2] = P - U;   // SW
+    o[1] = Q - V;   // NW
+    o[3] = Q + V;   // SE
+}
+
+// Scaled equilibrium out_i = scale * f_eq,i (Eqs. 4-7) in factored form: the raw
+// moments of the Maxwellian (binomial shift of the central moments of Eq. 5 by u)
+// times the parity-blocked inverse of M(0).  Inputs: rho, E = sum f (v^2+eta^2),
+// j = rho u, u, rho u^2, j_y u_y, P = rho T and T.
+__device__ __forceinline__ void equilibrium(const EqBlocks &B, const ModelConsts &m, double rho,
+                                            double E, double jx, double jy, double ux, double uy,
+                                            double ru2, double jyuy, double P, double T,
+                                            double out[kNV])
+{
+    const double ux2 = ux * ux, uy2 = uy * uy, u2 = ux2 + uy2;
+    const double m57 = fma(2.0, P, ru2);                                    // m5 + m7
+    const double m1416 = fma(T, fma(m.Kp6, ru2, m.twoKp2 * P), ru2 * u2);  // m14 + m16
+    const double W4 = fma(m.Kp4, T, u2);
+    const double d57 = fma(jx, ux, -jyuy);                                  // m5 - m7
+    const double d1416 = d57 * W4;                                          // m14 - m16
+    const double m6 = jx * uy;
+    const double m15 = m6 * W4;
+    const double W2 = fma(m.Kp2, T, u2);
+    const double m8 = jx * W2, m9 = jy * W2;
+    const double m10 = jx * fma(3.0, T, ux2);
+    const double m12 = jx * (uy2 + T);
+    const double m11 = jy * (ux2 + T);
+    const double m13 = jy * fma(3.0, T, uy2);
+    double s0[4], sx[4], sy[4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const double *S = B.S + 4 * g;
+        const double *V = B.V + 4 * g;
+        s0[g] = fma(S[3], m1416, fma(S[2], m57, fma(S[1], E, S[0] * rho)));
+        sx[g] = fma(V[3], m12, fma(V[2], m10, fma(V[1], m8, V[0] * jx)));
+        sy[g] = fma(V[3], m11, fma(V[2], m13, fma(V[1], m9, V[0] * jy)));
+    }
+    const double dqa = fma(B.B1[1], d1416, B.B1[0] * d57);
+    const double dqc = fma(B.B1[3], d1416, B.B1[2] * d57);
+    const double qb = fma(B.B2[1], m15, B.B2[0] * m6);
+    const double qd = fma(B.B2[3], m15, B.B2[2] * m6);
+    rebuild_axis(out + 0, s0[0], dqa, sx[0], sy[0]);
+    rebuild_diag(out + 4, s0[1], qb, sx[1], sy[1]);
+    rebuild_axis(out + 8, s0[2], dqc, sx[2], sy[2]);
+    rebuild_diag(out + 12, s0[3], qd, sx[3], sy[3]);
+}
+
+// Neighbour index along an axis of n cells: periodic wrap or zero-gradient clamp.
+__device__ __forceinline__ int neighbour(int j, int n, int bc)
+{
+    if (bc == 0) {
+        j %= n;
+        return j < 0 ? j + n : j;
+    }
+    return j < 0 ? 0 : (j >= n ? n - 1 : j);
+}
+
+}  // namespace cdbm

@@ -1,0 +1,82 @@
+// Internal declarations shared by the CDBM library's translation units (host API
+// and kernels).  Not part of the public ABI (include/cdbm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+
+namespace cdbm {
+
+constexpr int kNV = 16;     // discrete velocities, Eq. (2)
+
+// Parity-blocked inverse of the moment matrix at u = 0, pre-multiplied by the
+// factors that rebuild f_i from its group components and by a caller scale
+// (gamma * dt / tau inside a Runge-Kutta stage, 1 for plain f_eq).
+//
+// Per group g the four members split into
+//   s0 = sum,  sx (x-odd),  sy (y-odd),  dq (axis: (E+W)-(N+S)) or q (diag: (NE+SW)-(NW+SE)),
+// and the 16 raw-moment rows of Eq. (6) at u = 0 decouple into blocks
+//   scalar  (s0_a..s0_d) <- (m1, m4, m5+m7, m14+m16)          4x4
+//   axis q. (dq_a, dq_c) <- (m5-m7, m14-m16)                    2x2
+//   diag q. (q_b, q_d)   <- (m6, m15)                           2x2
+//   x-odd   (sx_a..sx_d) <- (m2, m8, m10, m12)                  4x4
+//   y-odd   (sy_a..sy_d) <- (m3, m9, m13, m11)  (same matrix)   4x4
+struct EqBlocks {
+    double S[16];   // row-major 4x4
+    double B1[4];   // row-major 2x2
+    double B2[4];   // row-major 2x2
+    double V[16];   // row-major 4x4
+};
+
+struct ModelConsts {
+    double c[4];      // group speeds v_a..v_d
+    double w[4];      // |v_g|^2 + eta_g^2 (|v|^2 = c^2 on axes, 2c^2 on diagonals)
+    double invK;      // 1 / (D + I)
+    double K;         // D + I
+    double Kp2, Kp4, Kp6, twoKp2;   // K + 2, K + 4, K + 6, 2 (K + 2)
+};
+
+// One Runge-Kutta stage: out = a_base * base + a_self * g + eq(g) - sum_r l_r D_r(g),
+// i.e. alpha f^n + beta g + gamma dt L(g) with a_self = beta - gamma h, the
+// equilibrium blocks scaled by gamma h and l = gamma dt c_g / dr.
+struct StageArgs {
+    EqBlocks eq;
+    ModelConsts m;
+    double a_base;
+    double a_self;
+    double lx[4];
+    double ly[4];
+    int nx, ny;
+    int bc_x, bc_y;
+};
+
+struct FieldArgs {
+    EqBlocks eq;     // unscaled
+    ModelConsts m;
+    double vx[kNV], vy[kNV], eta[kNV];
+    int nx, ny;
+};
+
+// Error bits of the device flag word.
+constexpr unsigned kFlagNonPhys = 1u;
+
+// ---- launchers (cdbm_kernels.cu); each returns the launch error ----
+cudaError_t launch_init(const FieldArgs &a, const double *rho, const double *ux,
+                        const double *uy, const double *T, double *f, unsigned *flag,
+                        cudaStream_t s);
+cudaError_t launch_macros(const FieldArgs &a, const double *f, double *rho, double *ux,
+                          double *uy, double *T, cudaStream_t s);
+cudaError_t launch_tne(const FieldArgs &a, const double *f, double *out, cudaStream_t s);
+cudaError_t launch_sums(const FieldArgs &a, const double *f, double *partials, int nblocks,
+                        double *out4, cudaStream_t s);
+
+// Stage kernel selection and launch geometry, shared with the graph builder.
+struct StageLaunch {
+    void *func;
+    dim3 grid, block;
+};
+StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count);
+cudaError_t launch_stage(const StageLaunch &L, const double *g, const double *base, double *out,
+                         const StageArgs &a, unsigned *flag, cudaStream_t s);
+
+}  // namespace cdbm

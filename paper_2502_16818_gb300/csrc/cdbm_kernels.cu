@@ -1,0 +1,280 @@
+// CDBM kernels (double precision): initial equilibrium, the fused Runge-Kutta
+// stage, macroscopic fields, nonequilibrium moments and conserved sums.
+//
+// Layout: f[16][ny][nx] (velocity plane outermost, x fastest).  One thread owns
+// one cell; a block covers a run of cells along x of one row, so centre loads
+// and stores of a warp are coalesced 256-byte rows and the stencil neighbours
+// (x +- 1, 2 and the rows y +- 1, 2) are served from L1/L2.
+#include "cdbm_device.cuh"
+
+namespace cdbm {
+
+namespace {
+
+constexpr int kStageThreads = 128;
+
+// ---------------------------------------------------------------- init (K0)
+
+__global__ void __launch_bounds__(128) init_kernel(const FieldArgs a, const double *__restrict__ rho,
+                                                    const double *__restrict__ ux,
+                                                    const double *__restrict__ uy,
+                                                    const double *__restrict__ T,
+                                                    double *__restrict__ f, unsigned *flag)
+{
+    const size_t P = (size_t)a.nx * a.ny;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < P;
+         c += (size_t)gridDim.x * blockDim.x) {
+        const double r = rho[c], u = ux[c], v = uy[c], t = T[c];
+        const double jx = r * u, jy = r * v;
+        const double jyuy = jy * v;
+        const double ru2 = fma(jx, u, jyuy);
+        const double p = r * t;
+        const double E = fma(a.m.K, p, ru2);
+        double fe[kNV];
+        equilibrium(a.eq, a.m, r, E, jx, jy, u, v, ru2, jyuy, p, t, fe);
+        if (!(positive_finite(r) && positive_finite(t) && isfinite(u) && isfinite(v)))
+            atomicOr(flag, kFlagNonPhys);
+#pragma unroll
+        for (int i = 0; i < kNV; ++i) f[i * P + c] = fe[i];
+    }
+}
+
+// ------------------------------------------------------------ RK stage (K1/K2)
+
+// out = a_base base + a_self g + gamma h f_eq(g) - sum_r l_r D_r(g) for one cell:
+// macros -> equilibrium -> BGK -> NND transport of all 16 velocities -> update.
+template <bool kBase, bool kFlatY>
+__global__ void __launch_bounds__(kStageThreads) stage_kernel(const double *__restrict__ g,
+                                                              const double *base, double *out,
+                                                              const StageArgs a, unsigned *flag)
+{
+    const int nx = a.nx, ny = a.ny;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nx) return;
+    const size_t P = (size_t)nx * ny;
+    const int xm2 = neighbour(x - 2, nx, a.bc_x), xm1 = neighbour(x - 1, nx, a.bc_x);
+    const int xp1 = neighbour(x + 1, nx, a.bc_x), xp2 = neighbour(x + 2, nx, a.bc_x);
+    for (int y = blockIdx.y; y < ny; y += gridDim.y) {
+        const size_t row = (size_t)y * nx;
+        const size_t c = row + x;
+        size_t rm2 = 0, rm1 = 0, rp1 = 0, rp2 = 0;
+        if (!kFlatY) {
+            rm2 = (size_t)neighbour(y - 2, ny, a.bc_y) * nx + x;
+            rm1 = (size_t)neighbour(y - 1, ny, a.bc_y) * nx + x;
+            rp1 = (size_t)neighbour(y + 1, ny, a.bc_y) * nx + x;
+            rp2 = (size_t)neighbour(y + 2, ny, a.bc_y) * nx + x;
+        }
+        double f[kNV];
+#pragma unroll
+        for (int i = 0; i < kNV; ++i) f[i] = __ldg(g + i * P + c);
+
+        const Cons q = conserved(f, a.m);
+        const double r = rcp64(q.rho);
+        const double ux = q.jx * r, uy = q.jy * r;
+        const double jyuy = q.jy * uy;
+        const double ru2 = fma(q.jx, ux, jyuy);
+        const double p = (q.E - ru2) * a.m.invK;
+        const double T = p * r;
+        if (!(positive_finite(q.rho) && positive_finite(p))) atomicOr(flag, kFlagNonPhys);
+        double heq[kNV];
+        equilibrium(a.eq, a.m, q.rho, q.E, q.jx, q.jy, ux, uy, ru2, jyuy, p, T, heq);
+
+#pragma unroll
+        for (int i = 0; i < kNV; ++i) {
+            const int grp = i >> 2;
+            const double *gp = g + i * P;
+            double o = fma(a.a_self, f[i], heq[i]);
+            if (kBase) o = fma(a.a_base, base[i * P + c], o);
+            if (dirx(i) != 0) {
+                const double u2 = __ldg(gp + row + (dirx(i) > 0 ? xm2 : xp2));
+                const double u1 = __ldg(gp + row + (dirx(i) > 0 ? xm1 : xp1));
+                const double d1 = __ldg(gp + row + (dirx(i) > 0 ? xp1 : xm1));
+                o = fma(-a.lx[grp], nnd(u2, u1, f[i], d1), o);
+            }
+            if (!kFlatY && diry(i) != 0) {
+                const double u2 = __ldg(gp + (diry(i) > 0 ? rm2 : rp2));
+                const double u1 = __ldg(gp + (diry(i) > 0 ? rm1 : rp1));
+                const double d1 = __ldg(gp + (diry(i) > 0 ? rp1 : rm1));
+                o = fma(-a.ly[grp], nnd(u2, u1, f[i], d1), o);
+            }
+            out[i * P + c] = o;
+        }
+    }
+}
+
+// ------------------------------------------------------------ macros (K3)
+
+__global__ void __launch_bounds__(128) macros_kernel(const FieldArgs a, const double *__restrict__ f,
+                                                      double *rho, double *ux, double *uy, double *T)
+{
+    const size_t P = (size_t)a.nx * a.ny;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < P;
+         c += (size_t)gridDim.x * blockDim.x) {
+        double fc[kNV];
+#pragma unroll
+        for (int i = 0; i < kNV; ++i) fc[i] = f[i * P + c];
+        const Cons q = conserved(fc, a.m);
+        const double u = q.jx / q.rho, v = q.jy / q.rho;
+        const double ru2 = fma(q.jx, u, q.jy * v);
+        if (rho) rho[c] = q.rho;
+        if (ux) ux[c] = u;
+        if (uy) uy[c] = v;
+        if (T) T[c] = (q.E - ru2) / (a.m.K * q.rho);
+    }
+}
+
+// ------------------------------------------------------------ TNE (K4)
+
+// Rows 5..16 of M(u) (Eq. 6) applied to f - f_eq: Delta* of Eqs. (8)-(11).
+__global__ void __launch_bounds__(128) tne_kernel(const FieldArgs a, const double *__restrict__ f,
+                                                   double *__restrict__ out)
+{
+    const size_t P = (size_t)a.nx * a.ny;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < P;
+         c += (size_t)gridDim.x * blockDim.x) {
+        double fc[kNV];
+#pragma unroll
+        for (int i = 0; i < kNV; ++i) fc[i] = f[i * P + c];
+        const Cons q = conserved(fc, a.m);
+        const double u = q.jx / q.rho, v = q.jy / q.rho;
+        const double jyuy = q.jy * v;
+        const double ru2 = fma(q.jx, u, jyuy);
+        const double p = (q.E - ru2) * a.m.invK;
+        const double T = p / q.rho;
+        double fe[kNV];
+        equilibrium(a.eq, a.m, q.rho, q.E, q.jx, q.jy, u, v, ru2, jyuy, p, T, fe);
+        double acc[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k] = 0.0;
+#pragma unroll
+        for (int i = 0; i < kNV; ++i) {
+            const double d = fc[i] - fe[i];
+            const double cx = a.vx[i] - u, cy = a.vy[i] - v;
+            const double cxx = cx * cx, cxy = cx * cy, cyy = cy * cy;
+            const double w = fma(a.eta[i], a.eta[i], cxx + cyy);
+            const double dw = d * w;
+            acc[0] = fma(d, cxx, acc[0]);
+            acc[1] = fma(d, cxy, acc[1]);
+            acc[2] = fma(d, cyy, acc[2]);
+            acc[3] = fma(dw, cx, acc[3]);
+            acc[4] = fma(dw, cy, acc[4]);
+            acc[5] = fma(d * cxx, cx, acc[5]);
+            acc[6] = fma(d * cxx, cy, acc[6]);
+            acc[7] = fma(d * cyy, cx, acc[7]);
+            acc[8] = fma(d * cyy, cy, acc[8]);
+            acc[9] = fma(dw, cxx, acc[9]);
+            acc[10] = fma(dw, cxy, acc[10]);
+            acc[11] = fma(dw, cyy, acc[11]);
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) out[k * P + c] = acc[k];
+    }
+}
+
+// ------------------------------------------------------------ sums (K5)
+
+constexpr int kSumThreads = 256;
+
+// Block b reduces cells [b*chunk, (b+1)*chunk) in a fixed order and writes its
+// four partial sums; the order depends only on the grid size and nblocks.
+__global__ void __launch_bounds__(kSumThreads) sums_partial_kernel(const FieldArgs a,
+                                                                   const double *__restrict__ f,
+                                                                   double *__restrict__ partials)
+{
+    __shared__ double sh[4][kSumThreads];
+    const size_t P = (size_t)a.nx * a.ny;
+    const size_t chunk = (P + gridDim.x - 1) / gridDim.x;
+    const size_t lo = blockIdx.x * chunk;
+    const size_t hi = lo + chunk < P ? lo + chunk : P;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (size_t c = lo + threadIdx.x; c < hi; c += kSumThreads) {
+        double fc[kNV];
+#pragma unroll
+        for (int i = 0; i < kNV; ++i) fc[i] = f[i * P + c];
+        const Cons q = conserved(fc, a.m);
+        s[0] += q.rho;
+        s[1] += q.jx;
+        s[2] += q.jy;
+        s[3] += q.E;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int w = kSumThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) partials[blockIdx.x * 4 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void sums_final_kernel(const double *__restrict__ partials, int nblocks, double *out4)
+{
+    if (threadIdx.x < 4) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks; ++b) s += partials[b * 4 + threadIdx.x];
+        out4[threadIdx.x] = s;
+    }
+}
+
+unsigned grid_for(size_t cells, int threads)
+{
+    size_t b = (cells + threads - 1) / threads;
+    return (unsigned)(b < 1 ? 1 : (b > 1048576 ? 1048576 : b));
+}
+
+}  // namespace
+
+cudaError_t launch_init(const FieldArgs &a, const double *rho, const double *ux, const double *uy,
+                        const double *T, double *f, unsigned *flag, cudaStream_t s)
+{
+    init_kernel<<<grid_for((size_t)a.nx * a.ny, 128), 128, 0, s>>>(a, rho, ux, uy, T, f, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macros(const FieldArgs &a, const double *f, double *rho, double *ux, double *uy,
+                          double *T, cudaStream_t s)
+{
+    macros_kernel<<<grid_for((size_t)a.nx * a.ny, 128), 128, 0, s>>>(a, f, rho, ux, uy, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tne(const FieldArgs &a, const double *f, double *out, cudaStream_t s)
+{
+    tne_kernel<<<grid_for((size_t)a.nx * a.ny, 128), 128, 0, s>>>(a, f, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sums(const FieldArgs &a, const double *f, double *partials, int nblocks,
+                        double *out4, cudaStream_t s)
+{
+    sums_partial_kernel<<<nblocks, kSumThreads, 0, s>>>(a, f, partials);
+    sums_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, out4);
+    return cudaGetLastError();
+}
+
+StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count)
+{
+    StageLaunch L;
+    const bool flat = (a.ny == 1);
+    if (with_base)
+        L.func = flat ? (void *)stage_kernel<true, true> : (void *)stage_kernel<true, false>;
+    else
+        L.func = flat ? (void *)stage_kernel<false, true> : (void *)stage_kernel<false, false>;
+    // Small grids: narrower blocks so that more SMs share the cells.
+    int threads = kStageThreads;
+    const size_t cells = (size_t)a.nx * a.ny;
+    while (threads > 32 && cells < (size_t)sm_count * threads * 2) threads >>= 1;
+    L.block = dim3(threads, 1, 1);
+    L.grid = dim3((a.nx + threads - 1) / threads, a.ny < 65535 ? a.ny : 65535, 1);
+    return L;
+}
+
+cudaError_t launch_stage(const StageLaunch &L, const double *g, const double *base, double *out,
+                         const StageArgs &a, unsigned *flag, cudaStream_t s)
+{
+    void *args[] = {(void *)&g, (void *)&base, (void *)&out, (void *)&a, (void *)&flag};
+    return cudaLaunchKernel(L.func, L.grid, L.block, args, 0, s);
+}
+
+}  // namespace cdbm

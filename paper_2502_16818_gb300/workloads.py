@@ -126,10 +126,11 @@ def taylor_green(n: int = 4096, I: float = 3.0, steps: int = 2000, dt: float | N
     """Taylor-Green vortex on the periodic square [0, 2L]^2 with k = pi / L:
     u = U0 sin(kx) cos(ky), v = -U0 cos(kx) sin(ky), rho = rho0,
     p = p0 + rho0 U0^2 / 4 (cos 2kx + cos 2ky), T = p / rho.
-    The default dt keeps max(|v_x| + |v_y|) dt / dx at 0.82 for n = 4096."""
+    The default dt is 5e-6 at n = 4096 (max(|v_x| + |v_y|) dt / dx = 0.82) and grows
+    with the cell size on coarser grids, capped at tau / 2."""
     dx = 2 * L / n
     if dt is None:
-        dt = 5e-6 * 4096.0 / n
+        dt = min(5e-6 * 4096.0 / n, 0.5 * tau)
     k = math.pi / L
     x = _centres(n, dx)
     X, Y = np.meshgrid(x, x, indexing="xy")   # [ny][nx]

@@ -404,6 +404,35 @@ def test_sound_speed_1d(I):
     assert abs(om / om_ref - 1) < 2e-3, (om, om_ref)
 
 
+@pytest.mark.parametrize("axis", ["x", "y"])
+def test_sound_speed_anisotropic_cells(axis):
+    """A 1-D standing wave along one axis of a grid whose cells are 7 times longer in
+    the other direction: the frequency depends only on the spacing along the wave."""
+    n, I, dt, tau = 96, 1.0, 2.5e-4, 2.5e-4
+    w = W.sound(n=n, ny=1, I=I, dt=dt, tau=tau)
+    if axis == "x":
+        m = model_of(w, ny=2, dy=7.0 / n)
+        fields = [np.repeat(a, 2, axis=0) for a in (w.rho, w.ux, w.uy, w.T)]
+    else:
+        m = model_of(w, nx=2, ny=n, dx=7.0 / n, dy=1.0 / n)
+        fields = [np.repeat(a.reshape(n, 1), 2, axis=1) for a in (w.rho, w.ux, w.uy, w.T)]
+    f = oracle.init(m, *fields)
+    x = (np.arange(n) + 0.5) / n
+    om_ref = math.sqrt(W.gamma_of(I)) * 2 * np.pi
+    steps = int(1.3 * 2 * math.pi / om_ref / dt) + 2
+    amps = [0.0]
+    for _ in range(steps):
+        f = oracle.step(m, f, 1)
+        _, ux, uy, _ = oracle.macros(m, f)
+        u = ux[0] if axis == "x" else uy[:, 0]
+        amps.append(float((u * np.cos(2 * np.pi * x)).sum()))
+    a = np.array(amps)
+    zc = [(i - a[i] / (a[i + 1] - a[i])) * dt for i in range(1, len(a) - 1)
+          if a[i] != 0 and np.sign(a[i]) != np.sign(a[i + 1])]
+    om = math.pi / (zc[1] - zc[0])
+    assert abs(om / om_ref - 1) < 3e-3, (axis, om, om_ref)
+
+
 @pytest.mark.slow
 def test_sound_speed_2d():
     om, om_ref = _sound_frequency(32, 32, 3.0, tau=4e-4, dt=4e-4)
