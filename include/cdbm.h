@@ -169,11 +169,44 @@ cdbm_status cdbm_time(const cdbm_ctx *ctx, double *t);
 cdbm_status cdbm_sync(cdbm_ctx *ctx);
 
 /* One-line description of the sticky error of ctx (NULL ctx: of the last failed
- * cdbm_create on this thread).  Never NULL. */
+ * cdbm_create or cdbm_step_noalloc on this thread).  Never NULL. */
 const char *cdbm_last_error(const cdbm_ctx *ctx);
 
 /* Releases the context and its device memory (stream-ordered).  NULL is a no-op. */
 void cdbm_destroy(cdbm_ctx *ctx);
+
+/* Largest grid (nx * ny cells) that cdbm_step_noalloc accepts. */
+#define CDBM_NOALLOC_MAX_CELLS 32768
+
+/*
+ * cdbm_step_noalloc -- cdbm_step without a context and without allocating anything.
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory -- a host code that owns all GPU memory through its own
+ * pool and forbids other allocations inside its time loop, a plug-in that is handed
+ * device buffers but no allocator, or a loop where cudaMalloc's implicit device
+ * synchronisation is not acceptable.
+ *   grid, vset, I, tau, dt : as for cdbm_create, with the same validation.
+ *   f            : device pointer to the caller's state [16][ny][nx] (for example from
+ *                  cdbm_get_state or an equilibrium the caller built), advanced in
+ *                  place by nsteps >= 0 two-stage TVD Runge-Kutta steps; the result
+ *                  equals cdbm_step's on the same state.
+ *   cuda_stream  : stream for the work (NULL = legacy stream).
+ * Scratch: the stage-1 buffer and the error flag live in one fixed device array of
+ * the library (16 * CDBM_NOALLOC_MAX_CELLS doubles plus 256 bytes, i.e. 4 MiB), which
+ * every GPU that loads the library holds until the process exits.  The call makes no
+ * cudaMalloc/cudaFree or other allocating call.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress, with the device current); make
+ * that first call before any stream capture.  All calls on a device share the array
+ * and it keeps the last call's contents (the flag is cleared at the start of each
+ * call), so calls that overlap on the GPU -- on different streams or host threads --
+ * race and must be serialised by the caller.
+ * Synchronous: returns after the work has finished.  Errors: CDBM_EINVAL (as
+ * cdbm_create, f NULL, nsteps < 0, or nx * ny > CDBM_NOALLOC_MAX_CELLS),
+ * CDBM_ESINGULAR, CDBM_ECUDA, CDBM_ENONPHYS (the state went non-physical; f holds the
+ * result of the last step).  Messages go to cdbm_last_error(NULL).
+ */
+cdbm_status cdbm_step_noalloc(const cdbm_grid *grid, const cdbm_vset *vset, double I, double tau,
+                              double dt, double *f, int nsteps, void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -26,7 +26,8 @@ CDBM_RK2_TVD, CDBM_RK2_MIDPOINT = 0, 1
 #: every entry point declared in include/cdbm.h
 EXPORTS = ("cdbm_create", "cdbm_set_rk", "cdbm_init", "cdbm_step", "cdbm_macros", "cdbm_tne",
            "cdbm_conserved_sums", "cdbm_get_state", "cdbm_set_state", "cdbm_state_ptr", "cdbm_time",
-           "cdbm_sync", "cdbm_last_error", "cdbm_destroy")
+           "cdbm_sync", "cdbm_last_error", "cdbm_destroy", "cdbm_step_noalloc")
+CDBM_NOALLOC_MAX_CELLS = 32768
 
 
 class cdbm_grid(ctypes.Structure):
@@ -88,6 +89,8 @@ def load(path: str | None = None):
         "cdbm_sync": ([ctx], ctypes.c_int),
         "cdbm_last_error": ([ctx], ctypes.c_char_p),
         "cdbm_destroy": ([ctx], None),
+        "cdbm_step_noalloc": ([ctypes.POINTER(cdbm_grid), ctypes.POINTER(cdbm_vset), ctypes.c_double,
+                               ctypes.c_double, ctypes.c_double, _vp, ctypes.c_int, _vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -184,6 +187,15 @@ def cdbm_last_error(ctx) -> str:
 
 def cdbm_destroy(ctx):
     load().cdbm_destroy(ctx)
+
+
+def cdbm_step_noalloc(grid: cdbm_grid, vset: cdbm_vset, I, tau, dt, f, nsteps, stream=0):
+    """Advances the caller's device state f ([16][ny][nx], address as int) in place
+    without any allocation; see include/cdbm.h."""
+    lib = load()
+    st = lib.cdbm_step_noalloc(ctypes.byref(grid), ctypes.byref(vset), float(I), float(tau),
+                               float(dt), ctypes.c_void_p(f), int(nsteps), ctypes.c_void_p(stream))
+    _check(lib, None, st)
 
 
 # ------------------------------------------------------------------ Solver

@@ -14,7 +14,7 @@ using namespace cdbm;
 
 namespace {
 
-thread_local char g_create_error[256] = "no error";
+thread_local char g_create_error[kThreadErrorBytes] = "no error";
 
 constexpr int kGraphSteps = 32;       // time steps per replayed CUDA graph
 constexpr double kMaxCond = 1e12;     // condition limit of the moment blocks
@@ -131,6 +131,10 @@ bool is_device_pointer(const void *p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+}  // namespace
+
+namespace cdbm {
+
 // In-place Gauss-Jordan inverse with partial pivoting; cond = ||A||_inf ||A^-1||_inf.
 bool invert(int n, const double *A, double *Ainv, double *cond)
 {
@@ -246,6 +250,8 @@ cdbm_status build_blocks(const cdbm_vset &vs, double I, ModelConsts &m, EqBlocks
     return CDBM_OK;
 }
 
+char *thread_error_buffer() { return g_create_error; }
+
 EqBlocks scaled(const EqBlocks &e, double s)
 {
     EqBlocks o;
@@ -259,6 +265,10 @@ EqBlocks scaled(const EqBlocks &e, double s)
     }
     return o;
 }
+
+}  // namespace cdbm
+
+namespace {
 
 void build_stages(cdbm_ctx *c)
 {

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 
+#include "../../include/cdbm.h"
+
 namespace cdbm {
 
 constexpr int kNV = 16;     // discrete velocities, Eq. (2)
@@ -59,6 +61,18 @@ struct FieldArgs {
 
 // Error bits of the device flag word.
 constexpr unsigned kFlagNonPhys = 1u;
+
+// ---- host-side constants (cdbm_api.cu) ----
+// Model constants and the parity-blocked inverse of M(0) for a velocity set and I;
+// CDBM_ESINGULAR with *which naming the block when a block is singular or its
+// condition number exceeds 1e12.
+cdbm_status build_blocks(const cdbm_vset &vs, double I, ModelConsts &m, EqBlocks &eq,
+                         double *cond_out, const char **which);
+EqBlocks scaled(const EqBlocks &e, double s);
+
+// Per-thread message buffer that cdbm_last_error(NULL) returns.
+constexpr size_t kThreadErrorBytes = 256;
+char *thread_error_buffer();
 
 // ---- launchers (cdbm_kernels.cu); each returns the launch error ----
 cudaError_t launch_init(const FieldArgs &a, const double *rho, const double *ux,
