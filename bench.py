@@ -46,14 +46,18 @@ FP64_LANES_PER_CLK_PER_SM = 2       # 1.25 TFLOP/s nominal FP64 / (2 flops x 152
 # the stage kernels; valid only while the kernel sources hash to TRAFFIC_SHA.
 # Captured at 1024^2 (134 MB per plane set, above L2) and scaled by 16 cells-fold; see
 # profiles/stage_kernel_tgv.md.
-TRAFFIC_SHA = "d051db640608e2e9"
+TRAFFIC_SHA = "11a587991b9001d0"
 TRAFFIC_BYTES_PER_LAUNCH = 4.784e9
 
 
+STAGE_SOURCES = ("cdbm_device.cuh", "cdbm_kernels.cu")
+
+
 def kernel_sha():
+    """Hash of the sources that define the stage kernels."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2502_16818_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in STAGE_SOURCES:
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(name.encode() + fh.read())
     return h.hexdigest()[:16]
