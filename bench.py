@@ -33,12 +33,13 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-updates/s and HBM GB/s vs FP64 plain on same GB300 at stated L2 error"
 UNIT = "cell-updates/s"
 
-# FP64 work of the fused stage kernels per cell (counted from the kernel source;
-# an FMA counts as two flops).  Stage 1: 317 FP64 instructions / 442 flops;
-# stage 2: 333 / 474.  Bytes per cell-step: stage 1 reads f^n and writes f1
-# (128 + 128 B); stage 2 reads f1 and f^n and writes f^n+1 (384 B).
-FP64_INSTR_PER_CELL_STEP = 650
-FP64_FLOPS_PER_CELL_STEP = 916
+# FP64 work of the fused stage kernels per cell.  Instructions: ncu
+# sm__inst_executed_pipe_fp64 per warp of 32 cells (stage 1: 293, stage 2: 309).
+# Flops, counted from the kernel source with an FMA as two flops: stage 1: 424,
+# stage 2: 456.  Bytes per cell-step: stage 1 reads f^n and writes f1 (128 + 128 B);
+# stage 2 reads f1 and f^n and writes f^n+1 (384 B).
+FP64_INSTR_PER_CELL_STEP = 602
+FP64_FLOPS_PER_CELL_STEP = 880
 BYTES_PER_CELL_STEP = 640
 FP64_LANES_PER_CLK_PER_SM = 2       # 1.25 TFLOP/s nominal FP64 / (2 flops x 152 SMs x 2.07 GHz)
 

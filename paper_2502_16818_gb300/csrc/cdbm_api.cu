@@ -236,12 +236,20 @@ cdbm_status build_blocks(const cdbm_vset &vs, double I, ModelConsts &m, EqBlocks
         worst = cond[b] > worst ? cond[b] : worst;
     }
     *cond_out = worst;
+    // Fold the raw Maxwellian moments into the coefficients (layout in EqBlocks):
+    // m5 + m7 = (2/K) E + (1 - 2/K) rho u^2; the odd rows are j times quadratics
+    // in (u_x^2, u_y^2, T); m14 - m16 and m15 are (m5 - m7) and m6 times W4.
     for (int g = 0; g < 4; ++g) {
         const double fv = (g & 1) ? 0.25 : 0.5;
-        for (int k = 0; k < 4; ++k) {
-            eq.S[g * 4 + k] = 0.25 * SI[g * 4 + k];
-            eq.V[g * 4 + k] = fv * VI[g * 4 + k];
-        }
+        const double *s = SI + 4 * g, *v = VI + 4 * g;
+        eq.S[g * 4 + 0] = 0.25 * s[0];
+        eq.S[g * 4 + 1] = 0.25 * (s[1] + (2.0 / K) * s[2]);
+        eq.S[g * 4 + 2] = 0.25 * (1.0 - 2.0 / K) * s[2];
+        eq.S[g * 4 + 3] = 0.25 * s[3];
+        eq.V[g * 4 + 0] = fv * v[0];
+        eq.V[g * 4 + 1] = fv * (v[1] + v[2]);
+        eq.V[g * 4 + 2] = fv * (v[1] + v[3]);
+        eq.V[g * 4 + 3] = fv * ((K + 2.0) * v[1] + 3.0 * v[2] + v[3]);
     }
     for (int k = 0; k < 4; ++k) {
         eq.B1[k] = 0.25 * B1I[k];

@@ -24,25 +24,31 @@ __host__ __device__ constexpr int diry(int i)
                                : (((i & 3) <= 1) ? 1 : -1);
 }
 
-// true iff v > 0 and v is finite (sign, zero and exponent tested on the bits).
+// true iff v > 0 and v is finite (sign, zero and exponent tested on the bits of
+// the two 32-bit halves, which keeps the test on the integer pipe).
 __device__ __forceinline__ bool positive_finite(double v)
 {
-    const long long b = __double_as_longlong(v);
-    return b > 0 && b < 0x7ff0000000000000LL;
+    const int h = __double2hiint(v);
+    const unsigned l = (unsigned)__double2loint(v);
+    return h >= 0 && h < 0x7ff00000 && ((unsigned)h | l) != 0u;
 }
 
 // minmod of Eq. (16) on the integer pipe: zero when either argument is zero or
 // the signs differ, otherwise the argument of smaller magnitude (X on a tie).
 // Magnitudes of finite doubles order like their bit patterns without the sign.
+// The tests work on the 32-bit halves: written on 64-bit integers they are turned
+// back into FP64 compares by the compiler, which costs three FP64 instructions per
+// transport difference on a GPU where the FP64 pipe is the bottleneck.
 __device__ __forceinline__ double minmod(double X, double Y)
 {
-    const long long x = __double_as_longlong(X);
-    const long long y = __double_as_longlong(Y);
-    const long long ax = x & 0x7fffffffffffffffLL;
-    const long long ay = y & 0x7fffffffffffffffLL;
-    const long long pick = (ax <= ay) ? x : y;
-    const bool keep = ((x ^ y) >= 0) & (ax != 0) & (ay != 0);
-    return __longlong_as_double(keep ? pick : 0LL);
+    const int hx = __double2hiint(X), lx = __double2loint(X);
+    const int hy = __double2hiint(Y), ly = __double2loint(Y);
+    const unsigned ahx = (unsigned)hx & 0x7fffffffu, ahy = (unsigned)hy & 0x7fffffffu;
+    const bool x_le_y = (ahx < ahy) | ((ahx == ahy) & ((unsigned)lx <= (unsigned)ly));
+    const bool keep = ((hx ^ hy) >= 0) & ((ahx | (unsigned)lx) != 0u) & ((ahy | (unsigned)ly) != 0u);
+    const int rh = keep ? (x_le_y ? hx : hy) : 0;
+    const int rl = keep ? (x_le_y ? lx : ly) : 0;
+    return __hiloint2double(rh, rl);
 }
 
 // NND transport difference (Eqs. 12-20) in upwind order.  For a velocity
@@ -121,7 +127,8 @@ __device__ __forceinline__ void rebuild_diag(double *o, double s0, double q, dou
 
 // Scaled equilibrium out_i = scale * f_eq,i (Eqs. 4-7) in factored form: the raw
 // moments of the Maxwellian (binomial shift of the central moments of Eq. 5 by u)
-// times the parity-blocked inverse of M(0).  Inputs: rho, E = sum f (v^2+eta^2),
+// times the parity-blocked inverse of M(0), with the moment products folded into
+// the block coefficients (see EqBlocks).  Inputs: rho, E = sum f (v^2+eta^2),
 // j = rho u, u, rho u^2, j_y u_y, P = rho T and T.
 __device__ __forceinline__ void equilibrium(const EqBlocks &B, const ModelConsts &m, double rho,
                                             double E, double jx, double jy, double ux, double uy,
@@ -129,32 +136,23 @@ __device__ __forceinline__ void equilibrium(const EqBlocks &B, const ModelConsts
                                             double out[kNV])
 {
     const double ux2 = ux * ux, uy2 = uy * uy, u2 = ux2 + uy2;
-    const double m57 = fma(2.0, P, ru2);                                    // m5 + m7
     const double m1416 = fma(T, fma(m.Kp6, ru2, m.twoKp2 * P), ru2 * u2);  // m14 + m16
     const double W4 = fma(m.Kp4, T, u2);
     const double d57 = fma(jx, ux, -jyuy);                                  // m5 - m7
-    const double d1416 = d57 * W4;                                          // m14 - m16
     const double m6 = jx * uy;
-    const double m15 = m6 * W4;
-    const double W2 = fma(m.Kp2, T, u2);
-    const double m8 = jx * W2, m9 = jy * W2;
-    const double m10 = jx * fma(3.0, T, ux2);
-    const double m12 = jx * (uy2 + T);
-    const double m11 = jy * (ux2 + T);
-    const double m13 = jy * fma(3.0, T, uy2);
     double s0[4], sx[4], sy[4];
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
         const double *S = B.S + 4 * g;
         const double *V = B.V + 4 * g;
-        s0[g] = fma(S[3], m1416, fma(S[2], m57, fma(S[1], E, S[0] * rho)));
-        sx[g] = fma(V[3], m12, fma(V[2], m10, fma(V[1], m8, V[0] * jx)));
-        sy[g] = fma(V[3], m11, fma(V[2], m13, fma(V[1], m9, V[0] * jy)));
+        s0[g] = fma(S[3], m1416, fma(S[2], ru2, fma(S[1], E, S[0] * rho)));
+        sx[g] = jx * fma(V[3], T, fma(V[2], uy2, fma(V[1], ux2, V[0])));
+        sy[g] = jy * fma(V[3], T, fma(V[1], uy2, fma(V[2], ux2, V[0])));
     }
-    const double dqa = fma(B.B1[1], d1416, B.B1[0] * d57);
-    const double dqc = fma(B.B1[3], d1416, B.B1[2] * d57);
-    const double qb = fma(B.B2[1], m15, B.B2[0] * m6);
-    const double qd = fma(B.B2[3], m15, B.B2[2] * m6);
+    const double dqa = d57 * fma(B.B1[1], W4, B.B1[0]);
+    const double dqc = d57 * fma(B.B1[3], W4, B.B1[2]);
+    const double qb = m6 * fma(B.B2[1], W4, B.B2[0]);
+    const double qd = m6 * fma(B.B2[3], W4, B.B2[2]);
     rebuild_axis(out + 0, s0[0], dqa, sx[0], sy[0]);
     rebuild_diag(out + 4, s0[1], qb, sx[1], sy[1]);
     rebuild_axis(out + 8, s0[2], dqc, sx[2], sy[2]);

@@ -23,6 +23,14 @@ constexpr int kNV = 16;     // discrete velocities, Eq. (2)
 //   diag q. (q_b, q_d)   <- (m6, m15)                           2x2
 //   x-odd   (sx_a..sx_d) <- (m2, m8, m10, m12)                  4x4
 //   y-odd   (sy_a..sy_d) <- (m3, m9, m13, m11)  (same matrix)   4x4
+// The raw Maxwellian moments are folded into the stored coefficients (host side):
+//   s0_g = S[g] . (rho, E, rho u^2, m14+m16)            (m5+m7 = (2E + (K-2) rho u^2) / K)
+//   dq   = (m5-m7) (B1[r][0] + B1[r][1] W4),  q = m6 (B2[r][0] + B2[r][1] W4),
+//          W4 = u^2 + (K+4) T                       (m14-m16 = (m5-m7) W4, m15 = m6 W4)
+//   sx_g = j_x (V[g][0] + V[g][1] u_x^2 + V[g][2] u_y^2 + V[g][3] T)
+//   sy_g = j_y (V[g][0] + V[g][2] u_x^2 + V[g][1] u_y^2 + V[g][3] T)
+//          (m8 = j_x (u^2 + (K+2)T), m10 = j_x (u_x^2 + 3T), m12 = j_x (u_y^2 + T), and
+//           the mirror images for y)
 struct EqBlocks {
     double S[16];   // row-major 4x4
     double B1[4];   // row-major 2x2

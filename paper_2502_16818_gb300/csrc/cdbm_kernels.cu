@@ -12,6 +12,9 @@ namespace cdbm {
 namespace {
 
 constexpr int kStageThreads = 128;
+#ifndef CDBM_STAGE_MIN_BLOCKS
+#define CDBM_STAGE_MIN_BLOCKS 3   // resident stage blocks per SM the register budget must allow
+#endif
 
 // ---------------------------------------------------------------- init (K0)
 
@@ -44,7 +47,7 @@ __global__ void __launch_bounds__(128) init_kernel(const FieldArgs a, const doub
 // out = a_base base + a_self g + gamma h f_eq(g) - sum_r l_r D_r(g) for one cell:
 // macros -> equilibrium -> BGK -> NND transport of all 16 velocities -> update.
 template <bool kBase, bool kFlatY>
-__global__ void __launch_bounds__(kStageThreads) stage_kernel(const double *__restrict__ g,
+__global__ void __launch_bounds__(kStageThreads, CDBM_STAGE_MIN_BLOCKS) stage_kernel(const double *__restrict__ g,
                                                               const double *base, double *out,
                                                               const StageArgs a, unsigned *flag)
 {
