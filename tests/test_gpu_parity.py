@@ -240,18 +240,28 @@ def test_taylor_green_128():
     assert_fields(got, ref, label="tgv128", gamma=W.gamma_of(3.0))
 
 
+def _axis_range(c, r, n, bc):
+    """Indices of the patch along one axis and the position of c in it: periodic
+    axes wrap; zero-gradient axes stop at the domain edge, where the patch's own
+    zero-gradient boundary is then the true one."""
+    if bc == W.PERIODIC:
+        return np.arange(c - r, c + r + 1) % n, r
+    lo, hi = max(0, c - r), min(n - 1, c + r)
+    return np.arange(lo, hi + 1), c - lo
+
+
 def _patch(w, cy, cx, r):
-    """Sub-problem of radius r around (cy, cx) taken from the initial fields, with
-    periodic indices; the oracle runs it with zero-gradient edges, which cannot
-    reach the centre within r/4 steps (stencil reach 2 per stage)."""
-    ys = np.arange(cy - r, cy + r + 1) % w.ny
-    xs = np.arange(cx - r, cx + r + 1) % w.nx
+    """Sub-problem of radius r around (cy, cx) taken from the initial fields; the
+    oracle runs it with zero-gradient edges, whose influence cannot reach the centre
+    within r/4 steps (stencil reach 2 per stage)."""
+    ys, py = _axis_range(cy, r, w.ny, w.bc_y)
+    xs, px = _axis_range(cx, r, w.nx, w.bc_x)
     sub = [a[np.ix_(ys, xs)] for a in (w.rho, w.ux, w.uy, w.T)]
-    m = model_of(w, nx=2 * r + 1, ny=2 * r + 1, bc_x=W.ZERO_GRADIENT, bc_y=W.ZERO_GRADIENT)
-    return m, sub
+    m = model_of(w, nx=len(xs), ny=len(ys), bc_x=W.ZERO_GRADIENT, bc_y=W.ZERO_GRADIENT)
+    return m, sub, py, px
 
 
-def _sampled_check(w, steps, nsamp, seed):
+def _sampled_check(w, steps, nsamp, seed, edges=False):
     s = solver(w)
     s.init(w.rho, w.ux, w.uy, w.T)
     s.step(steps)
@@ -263,18 +273,22 @@ def _sampled_check(w, steps, nsamp, seed):
     r = 4 * steps + 2
     pts = [(int(rng.integers(w.ny)), int(rng.integers(w.nx))) for _ in range(nsamp)]
     pts += [(0, 0), (w.ny - 1, w.nx - 1), (0, w.nx - 1)]
+    if edges:   # block and row-run boundaries: x = 127, 128; rows around multiples of 8
+        pts += [(8 * k + d, 128 * j + e) for k in (1, 40, 161) for d in (-1, 0)
+                for j in (1, 11) for e in (-1, 0) if 8 * k + d < w.ny and 128 * j + e < w.nx]
+        pts += [(w.ny - 1, 700), (w.ny - 2, w.nx - 2), (1, 1)]
     cs = math.sqrt(W.gamma_of(w.I) * float(np.mean(got[3])))
     us = max(np.abs(got[1]).max(), np.abs(got[2]).max(), cs)
     scale = [np.abs(got[0]).max(), us, us, np.abs(got[3]).max()]
     for (cy, cx) in pts:
-        m, sub = _patch(w, cy, cx, r)
+        m, sub, py, px = _patch(w, cy, cx, r)
         fo = oracle.step(m, oracle.init(m, *sub), steps)
         ref = oracle.macros(m, fo)
         for k, name in enumerate(FIELDS):
-            e = abs(got[k][cy, cx] - ref[k][r, r]) / scale[k]
+            e = abs(got[k][cy, cx] - ref[k][py, px]) / scale[k]
             assert e <= TOL, "%s at (%d,%d): %.3e" % (name, cy, cx, e)
         fcell = f_gpu[:, cy, cx].cpu().numpy()
-        assert np.abs(fcell - fo[:, r, r]).max() <= 1e-11 * np.abs(fo[:, r, r]).max()
+        assert np.abs(fcell - fo[:, py, px]).max() <= 1e-11 * np.abs(fo[:, py, px]).max()
 
 
 def test_sound_wave_512_sampled():
@@ -287,6 +301,18 @@ def test_taylor_green_4096_sampled():
     """Full 4096^2 Taylor-Green vortex in the launch configuration the benchmark
     times, 3 steps, sampled cells against oracle patches."""
     _sampled_check(W.taylor_green(n=4096, I=3.0), 3, 24, seed=4)
+
+
+@pytest.mark.parametrize("bc", [(W.PERIODIC, W.PERIODIC), (W.ZERO_GRADIENT, W.ZERO_GRADIENT)])
+def test_row_marching_kernel_ragged_sampled(bc):
+    """A 1500 x 1300 grid is large enough for the row-marching stage kernel; neither
+    size is a multiple of the block width (128) or of the row runs, so partial blocks
+    and runs cut short by the last row are checked at sampled cells and edges."""
+    w = W.random_blocks(1500, 1300, seed=31, bc=bc)
+    w.dx = w.dy = 1.0 / 1500
+    w.dt = 0.2 * w.dx / 2.2
+    w.tau = 2 * w.dt
+    _sampled_check(w, 3, 40, seed=5, edges=True)
 
 
 def test_taylor_green_4096_conservation():
