@@ -84,7 +84,11 @@ typedef struct {
 
 /* Precision of the stored state. */
 typedef enum {
-    CDBM_FP64 = 0         /* state, flux, equilibrium and sums in IEEE double      */
+    CDBM_FP64 = 0,        /* state, flux, equilibrium and sums in IEEE double      */
+    CDBM_FP32_BULK = 1    /* state f and the NND transport in IEEE single; the     */
+                          /* conserved sums, the moment shift and the equilibrium  */
+                          /* product in double; f_eq is rounded to single when it  */
+                          /* enters the stage update                               */
 } cdbm_precision;
 
 /* Time integrator.  The paper names a second-order Runge-Kutta scheme without
@@ -153,13 +157,15 @@ cdbm_status cdbm_tne(cdbm_ctx *ctx, double *out);
  */
 cdbm_status cdbm_conserved_sums(cdbm_ctx *ctx, double out[4]);
 
-/* Copies the state f ([16][ny][nx], host or device) and the time out / in. */
+/* Copies the state f ([16][ny][nx] doubles, host or device) and the time out / in;
+ * a CDBM_FP32_BULK state is widened on the way out and rounded on the way in. */
 cdbm_status cdbm_get_state(cdbm_ctx *ctx, double *f, double *t);
 cdbm_status cdbm_set_state(cdbm_ctx *ctx, const double *f, double t);
 
-/* Device pointer of the state f ([16][ny][nx] doubles, owned by the context,
- * valid until cdbm_destroy); steps update it in place. */
-cdbm_status cdbm_state_ptr(cdbm_ctx *ctx, double **f);
+/* Device pointer of the state f ([16][ny][nx], owned by the context, valid until
+ * cdbm_destroy; steps update it in place): doubles for CDBM_FP64, floats for
+ * CDBM_FP32_BULK. */
+cdbm_status cdbm_state_ptr(cdbm_ctx *ctx, void **f);
 
 /* Simulated time (host scalar). */
 cdbm_status cdbm_time(const cdbm_ctx *ctx, double *t);

@@ -50,8 +50,9 @@ struct cdbm_ctx {
     int sm_count;
 
     size_t plane;                 // nx * ny
-    double *f;                    // state [16][ny][nx]
-    double *f1;                   // stage buffer [16][ny][nx]; also staging for host I/O
+    void *f;                      // state [16][ny][nx] in storage precision
+    void *f1;                     // stage buffer [16][ny][nx] in storage precision; also
+                                  // double staging (16 planes) for host I/O and conversions
     double *partials;             // conserved-sum partials [nblocks][4]
     double *sums;                 // 4 doubles
     unsigned *flag;               // device error flags
@@ -62,6 +63,7 @@ struct cdbm_ctx {
 
     EqBlocks eq_unit;
     ModelConsts mc;
+    double Fg[4];                 // FP32-bulk reference equilibrium per group (0 for FP64)
     StageArgs stage[2];
     StageLaunch launch[2];
     RkStage rks[2];
@@ -278,6 +280,21 @@ EqBlocks scaled(const EqBlocks &e, double s)
 
 namespace {
 
+// Reference equilibrium F = f_eq(rho0, u = 0, T0) of the FP32-bulk deviation
+// storage: with u = 0 every member of group g equals the group sum times 1/4, which
+// the unit scalar block gives from (rho, E = K P, rho u^2 = 0, m14+m16 = 2 (K+2) P T).
+void set_reference(cdbm_ctx *c, double rho0, double T0)
+{
+    const double K = c->mc.K, P0 = rho0 * T0;
+    for (int g = 0; g < 4; ++g) {
+        const double *S = c->eq_unit.S + 4 * g;
+        c->Fg[g] = (c->precision == CDBM_FP32_BULK && std::isfinite(rho0) && std::isfinite(T0))
+                       ? S[0] * rho0 + S[1] * K * P0 + S[3] * 2.0 * (K + 2.0) * P0 * T0
+                       : 0.0;
+        c->fields.Fg[g] = c->Fg[g];
+    }
+}
+
 void build_stages(cdbm_ctx *c)
 {
     rk_stages(c->rk, c->rks);
@@ -293,11 +310,24 @@ void build_stages(cdbm_ctx *c)
             a.lx[g] = r.gamma * c->dt * c->mc.c[g] / c->grid.dx;
             a.ly[g] = r.gamma * c->dt * c->mc.c[g] / c->grid.dy;
         }
+        a.a_base_f = (float)a.a_base;
+        a.a_self_f = (float)a.a_self;
+        for (int g = 0; g < 4; ++g) {
+            a.lx_f[g] = (float)a.lx[g];
+            a.ly_f[g] = (float)a.ly[g];
+        }
+        a.rhoF = 0.0;
+        a.EF = 0.0;
+        for (int g = 0; g < 4; ++g) {
+            a.sF[g] = r.gamma * h * c->Fg[g];
+            a.rhoF += 4.0 * c->Fg[g];
+            a.EF += 4.0 * c->Fg[g] * c->mc.w[g];
+        }
         a.nx = c->grid.nx;
         a.ny = c->grid.ny;
         a.bc_x = c->grid.bc_x;
         a.bc_y = c->grid.bc_y;
-        c->launch[s] = stage_launch_config(a, r.with_base, c->sm_count);
+        c->launch[s] = stage_launch_config(a, r.with_base, c->sm_count, c->precision);
     }
 }
 
@@ -316,12 +346,12 @@ cdbm_status build_graph(cdbm_ctx *c)
     cudaGraph_t g;
     if (cudaGraphCreate(&g, 0) != cudaSuccess) return cuda_check(c, cudaGetLastError(), "graph create");
     cudaGraphNode_t prev = nullptr;
-    const double *nil = nullptr;
+    const void *nil = nullptr;
     for (int s = 0; s < kGraphSteps; ++s) {
         for (int k = 0; k < 2; ++k) {
-            const double *gin = (k == 0) ? c->f : c->f1;
-            const double *base = (k == 0) ? nil : c->f;
-            double *out = (k == 0) ? c->f1 : c->f;
+            const void *gin = (k == 0) ? c->f : c->f1;
+            const void *base = (k == 0) ? nil : c->f;
+            void *out = (k == 0) ? c->f1 : c->f;
             void *args[] = {(void *)&gin, (void *)&base, (void *)&out, (void *)&c->stage[k],
                             (void *)&c->flag};
             cudaKernelNodeParams p;
@@ -377,7 +407,8 @@ cdbm_status cdbm_create(const cdbm_grid *grid, const cdbm_vset *vset, double I, 
     if (!(std::isfinite(I) && I >= 0.0)) return create_err(CDBM_EINVAL, "I must be finite and >= 0");
     if ((grid->bc_x != 0 && grid->bc_x != 1) || (grid->bc_y != 0 && grid->bc_y != 1))
         return create_err(CDBM_EINVAL, "unknown boundary kind");
-    if (precision != CDBM_FP64) return create_err(CDBM_EINVAL, "unsupported precision %d", precision);
+    if (precision != CDBM_FP64 && precision != CDBM_FP32_BULK)
+        return create_err(CDBM_EINVAL, "unsupported precision %d", precision);
     for (int g = 0; g < 4; ++g)
         if (!std::isfinite(vset->v[g]) || !std::isfinite(vset->eta[g]) || vset->v[g] <= 0.0 ||
             vset->eta[g] < 0.0)
@@ -436,18 +467,19 @@ cdbm_status cdbm_create(const cdbm_grid *grid, const cdbm_vset *vset, double I, 
     c->fields.nx = grid->nx;
     c->fields.ny = grid->ny;
 
-    const size_t fbytes = sizeof(double) * kNV * c->plane;
-    c->f = (double *)ctx_alloc(c, fbytes);
-    c->f1 = (double *)ctx_alloc(c, fbytes);
+    const size_t fbytes = storage_bytes(precision) * kNV * c->plane;
+    const size_t f1bytes = sizeof(double) * kNV * c->plane;
+    c->f = ctx_alloc(c, fbytes);
+    c->f1 = ctx_alloc(c, f1bytes);
     c->partials = (double *)ctx_alloc(c, sizeof(double) * 4 * c->sum_blocks + sizeof(double) * 4 + 256);
     if (!c->f || !c->f1 || !c->partials || cudaMallocHost(&c->flag_host, sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();
         ctx_free(c, c->f, fbytes);
-        ctx_free(c, c->f1, fbytes);
+        ctx_free(c, c->f1, f1bytes);
         ctx_free(c, c->partials, 0);
         cudaStreamSynchronize(c->stream);
         delete c;
-        return create_err(CDBM_ENOMEM, "device allocation of %zu bytes failed", 2 * fbytes);
+        return create_err(CDBM_ENOMEM, "device allocation of %zu bytes failed", fbytes + f1bytes);
     }
     c->sums = c->partials + 4 * c->sum_blocks;
     c->flag = (unsigned *)(c->sums + 4);
@@ -489,14 +521,28 @@ cdbm_status cdbm_init(cdbm_ctx *c, const double *rho, const double *ux, const do
             dev[k] = src[k];
         } else {
             any_host = true;
-            double *dst = c->f1 + k * c->plane;
+            double *dst = (double *)c->f1 + k * c->plane;
             if (cuda_check(c, cudaMemcpyAsync(dst, src[k], bytes, cudaMemcpyHostToDevice, c->stream),
                            "cdbm_init upload"))
                 return c->err;
             dev[k] = dst;
         }
     }
-    if (cuda_check(c, launch_init(c->fields, dev[0], dev[1], dev[2], dev[3], c->f, c->flag, c->stream),
+    if (c->precision == CDBM_FP32_BULK) {
+        // reference state for the deviation storage: the means of rho and T
+        double sum[2] = {0.0, 0.0};
+        if (cuda_check(c, launch_field_means(dev[0], dev[3], c->plane, c->partials, c->sum_blocks, c->sums,
+                                             c->stream), "means launch") ||
+            cuda_check(c, cudaMemcpyAsync(sum, c->sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                       "means download") ||
+            cuda_check(c, cudaStreamSynchronize(c->stream), "means sync"))
+            return c->err;
+        set_reference(c, sum[0] / (double)c->plane, sum[1] / (double)c->plane);
+        drop_graph(c);
+        build_stages(c);
+    }
+    if (cuda_check(c, launch_init(c->fields, dev[0], dev[1], dev[2], dev[3], c->f, c->precision, c->flag,
+                                  c->stream),
                    "init launch"))
         return c->err;
     if (any_host && cuda_check(c, cudaStreamSynchronize(c->stream), "cdbm_init sync")) return c->err;
@@ -535,9 +581,9 @@ cdbm_status cdbm_macros(cdbm_ctx *c, double *rho, double *ux, double *uy, double
     for (int k = 0; k < 4; ++k) {
         host[k] = dst[k] && !is_device_pointer(dst[k]);
         any_host |= host[k];
-        dev[k] = host[k] ? c->f1 + k * c->plane : dst[k];
+        dev[k] = host[k] ? (double *)c->f1 + k * c->plane : dst[k];
     }
-    if (cuda_check(c, launch_macros(c->fields, c->f, dev[0], dev[1], dev[2], dev[3], c->stream),
+    if (cuda_check(c, launch_macros(c->fields, c->f, c->precision, dev[0], dev[1], dev[2], dev[3], c->stream),
                    "macros launch"))
         return c->err;
     for (int k = 0; k < 4; ++k)
@@ -556,8 +602,8 @@ cdbm_status cdbm_tne(cdbm_ctx *c, double *out)
     if (!out) return set_err(c, CDBM_EINVAL, "cdbm_tne: NULL output");
     if (!c->state_set) return set_err(c, CDBM_EINVAL, "cdbm_tne: state not initialised");
     const bool host = !is_device_pointer(out);
-    double *dev = host ? c->f1 : out;
-    if (cuda_check(c, launch_tne(c->fields, c->f, dev, c->stream), "tne launch")) return c->err;
+    double *dev = host ? (double *)c->f1 : out;
+    if (cuda_check(c, launch_tne(c->fields, c->f, c->precision, dev, c->stream), "tne launch")) return c->err;
     if (host) {
         if (cuda_check(c, cudaMemcpyAsync(out, dev, sizeof(double) * 12 * c->plane,
                                           cudaMemcpyDeviceToHost, c->stream), "cdbm_tne download") ||
@@ -573,7 +619,7 @@ cdbm_status cdbm_conserved_sums(cdbm_ctx *c, double out[4])
     if (c->err) return c->err;
     if (!out) return set_err(c, CDBM_EINVAL, "cdbm_conserved_sums: NULL output");
     if (!c->state_set) return set_err(c, CDBM_EINVAL, "cdbm_conserved_sums: state not initialised");
-    if (cuda_check(c, launch_sums(c->fields, c->f, c->partials, c->sum_blocks, c->sums, c->stream),
+    if (cuda_check(c, launch_sums(c->fields, c->f, c->precision, c->partials, c->sum_blocks, c->sums, c->stream),
                    "sums launch") ||
         cuda_check(c, cudaMemcpyAsync(out, c->sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
                    "sums download") ||
@@ -589,9 +635,19 @@ cdbm_status cdbm_get_state(cdbm_ctx *c, double *f, double *t)
     if (f) {
         if (!c->state_set) return set_err(c, CDBM_EINVAL, "cdbm_get_state: state not initialised");
         const bool host = !is_device_pointer(f);
-        if (cuda_check(c, cudaMemcpyAsync(f, c->f, sizeof(double) * kNV * c->plane, cudaMemcpyDefault,
-                                          c->stream), "cdbm_get_state copy"))
-            return c->err;
+        const size_t n = kNV * c->plane;
+        if (c->precision == CDBM_FP64) {
+            if (cuda_check(c, cudaMemcpyAsync(f, c->f, sizeof(double) * n, cudaMemcpyDefault, c->stream),
+                           "cdbm_get_state copy"))
+                return c->err;
+        } else {
+            double *dst = host ? (double *)c->f1 : f;
+            if (cuda_check(c, launch_convert(c->fields, c->f, c->precision, dst, CDBM_FP64, c->stream),
+                           "cdbm_get_state convert") ||
+                (host && cuda_check(c, cudaMemcpyAsync(f, dst, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                                                       c->stream), "cdbm_get_state copy")))
+                return c->err;
+        }
         if (host && cuda_check(c, cudaStreamSynchronize(c->stream), "cdbm_get_state sync")) return c->err;
     }
     if (t) *t = c->t;
@@ -604,16 +660,41 @@ cdbm_status cdbm_set_state(cdbm_ctx *c, const double *f, double t)
     if (c->err) return c->err;
     if (!f || !std::isfinite(t)) return set_err(c, CDBM_EINVAL, "cdbm_set_state: bad argument");
     const bool host = !is_device_pointer(f);
-    if (cuda_check(c, cudaMemcpyAsync(c->f, f, sizeof(double) * kNV * c->plane, cudaMemcpyDefault,
-                                      c->stream), "cdbm_set_state copy"))
-        return c->err;
+    const size_t n = kNV * c->plane;
+    if (c->precision == CDBM_FP64) {
+        if (cuda_check(c, cudaMemcpyAsync(c->f, f, sizeof(double) * n, cudaMemcpyDefault, c->stream),
+                       "cdbm_set_state copy"))
+            return c->err;
+    } else {
+        const double *src = f;
+        if (host) {
+            if (cuda_check(c, cudaMemcpyAsync(c->f1, f, sizeof(double) * n, cudaMemcpyHostToDevice,
+                                              c->stream), "cdbm_set_state copy"))
+                return c->err;
+            src = (const double *)c->f1;
+        }
+        // reference state from the mean conserved moments of the incoming state
+        double sum[4];
+        if (cuda_check(c, launch_sums(c->fields, src, CDBM_FP64, c->partials, c->sum_blocks, c->sums,
+                                      c->stream), "cdbm_set_state sums") ||
+            cuda_check(c, cudaMemcpyAsync(sum, c->sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                       "cdbm_set_state sums download") ||
+            cuda_check(c, cudaStreamSynchronize(c->stream), "cdbm_set_state sync"))
+            return c->err;
+        set_reference(c, sum[0] / (double)c->plane, sum[3] / (sum[0] * c->mc.K));
+        drop_graph(c);
+        build_stages(c);
+        if (cuda_check(c, launch_convert(c->fields, src, CDBM_FP64, c->f, c->precision, c->stream),
+                       "cdbm_set_state convert"))
+            return c->err;
+    }
     if (host && cuda_check(c, cudaStreamSynchronize(c->stream), "cdbm_set_state sync")) return c->err;
     c->t = t;
     c->state_set = true;
     return CDBM_OK;
 }
 
-cdbm_status cdbm_state_ptr(cdbm_ctx *c, double **f)
+cdbm_status cdbm_state_ptr(cdbm_ctx *c, void **f)
 {
     if (!c || !f) return CDBM_EINVAL;
     *f = c->f;
@@ -650,9 +731,8 @@ void cdbm_destroy(cdbm_ctx *c)
 {
     if (!c) return;
     drop_graph(c);
-    const size_t fbytes = sizeof(double) * kNV * c->plane;
-    ctx_free(c, c->f, fbytes);
-    ctx_free(c, c->f1, fbytes);
+    ctx_free(c, c->f, storage_bytes(c->precision) * kNV * c->plane);
+    ctx_free(c, c->f1, sizeof(double) * kNV * c->plane);
     ctx_free(c, c->partials, sizeof(double) * 4 * c->sum_blocks + sizeof(double) * 4 + 256);
     cudaStreamSynchronize(c->stream);
     if (c->flag_host) cudaFreeHost(c->flag_host);

@@ -66,6 +66,25 @@ __device__ __forceinline__ double nnd(double u2, double u1, double c, double d1)
     return fma(0.5, t, a);
 }
 
+// Single-precision twins of minmod() and nnd() for the FP32-bulk state: same
+// expressions, with the limiter decided on the float's bit pattern.
+__device__ __forceinline__ float minmod(float X, float Y)
+{
+    const int x = __float_as_int(X), y = __float_as_int(Y);
+    const unsigned ax = (unsigned)x & 0x7fffffffu, ay = (unsigned)y & 0x7fffffffu;
+    const bool keep = ((x ^ y) >= 0) & (ax != 0u) & (ay != 0u);
+    return __int_as_float(keep ? (ax <= ay ? x : y) : 0);
+}
+
+__device__ __forceinline__ float nnd(float u2, float u1, float c, float d1)
+{
+    const float a = c - u1;
+    const float b = d1 - c;
+    const float e = u1 - u2;
+    const float t = minmod(b, a) - minmod(a, e);
+    return fmaf(0.5f, t, a);
+}
+
 // 1 / a for a > 0: hardware estimate refined by one cubic Newton-Raphson step,
 // r (1 + e + e^2) with e = 1 - a r (error ~ e^3, below one ulp).
 __device__ __forceinline__ double rcp64(double a)
@@ -130,10 +149,13 @@ __device__ __forceinline__ void rebuild_diag(double *o, double s0, double q, dou
 // times the parity-blocked inverse of M(0), with the moment products folded into
 // the block coefficients (see EqBlocks).  Inputs: rho, E = sum f (v^2+eta^2),
 // j = rho u, u, rho u^2, j_y u_y, P = rho T and T.
+// With kShift, s0_shift[g] is subtracted from the group sums before the rebuild,
+// i.e. a reference equilibrium constant per group is taken off the result.
+template <bool kShift = false>
 __device__ __forceinline__ void equilibrium(const EqBlocks &B, const ModelConsts &m, double rho,
                                             double E, double jx, double jy, double ux, double uy,
                                             double ru2, double jyuy, double P, double T,
-                                            double out[kNV])
+                                            double out[kNV], const double *s0_shift = nullptr)
 {
     const double ux2 = ux * ux, uy2 = uy * uy, u2 = ux2 + uy2;
     const double m1416 = fma(T, fma(m.Kp6, ru2, m.twoKp2 * P), ru2 * u2);  // m14 + m16
@@ -146,6 +168,7 @@ __device__ __forceinline__ void equilibrium(const EqBlocks &B, const ModelConsts
         const double *S = B.S + 4 * g;
         const double *V = B.V + 4 * g;
         s0[g] = fma(S[3], m1416, fma(S[2], ru2, fma(S[1], E, S[0] * rho)));
+        if (kShift) s0[g] -= s0_shift[g];
         sx[g] = jx * fma(V[3], T, fma(V[2], uy2, fma(V[1], ux2, V[0])));
         sy[g] = jy * fma(V[3], T, fma(V[1], uy2, fma(V[2], ux2, V[0])));
     }

@@ -56,6 +56,15 @@ struct StageArgs {
     double a_self;
     double lx[4];
     double ly[4];
+    float a_base_f, a_self_f;     // the same coefficients rounded for the FP32-bulk state
+    float lx_f[4], ly_f[4];
+    // FP32-bulk state stores g = f - F, F the equilibrium of a constant reference
+    // state (rho0, u = 0, T0): F_i = Fg[group of i].  The stage adds F's conserved
+    // moments (rhoF, EF; F carries no momentum) to those of g and subtracts
+    // gamma h F from the equilibrium (sF = gamma h Fg); the F terms of the update
+    // cancel because alpha + beta = 1 in every stage.
+    double sF[4];
+    double rhoF, EF;
     int nx, ny;
     int bc_x, bc_y;
 };
@@ -64,6 +73,7 @@ struct FieldArgs {
     EqBlocks eq;     // unscaled
     ModelConsts m;
     double vx[kNV], vy[kNV], eta[kNV];
+    double Fg[4];    // reference equilibrium per group (FP32-bulk state only)
     int nx, ny;
 };
 
@@ -83,22 +93,35 @@ constexpr size_t kThreadErrorBytes = 256;
 char *thread_error_buffer();
 
 // ---- launchers (cdbm_kernels.cu); each returns the launch error ----
+// `prec` is the storage precision of the distribution buffers (CDBM_FP64 or
+// CDBM_FP32_BULK); fields, Delta* and sums are always double.
 cudaError_t launch_init(const FieldArgs &a, const double *rho, const double *ux,
-                        const double *uy, const double *T, double *f, unsigned *flag,
+                        const double *uy, const double *T, void *f, int prec, unsigned *flag,
                         cudaStream_t s);
-cudaError_t launch_macros(const FieldArgs &a, const double *f, double *rho, double *ux,
+cudaError_t launch_macros(const FieldArgs &a, const void *f, int prec, double *rho, double *ux,
                           double *uy, double *T, cudaStream_t s);
-cudaError_t launch_tne(const FieldArgs &a, const double *f, double *out, cudaStream_t s);
-cudaError_t launch_sums(const FieldArgs &a, const double *f, double *partials, int nblocks,
+cudaError_t launch_tne(const FieldArgs &a, const void *f, int prec, double *out, cudaStream_t s);
+cudaError_t launch_sums(const FieldArgs &a, const void *f, int prec, double *partials, int nblocks,
                         double *out4, cudaStream_t s);
+// Copies a whole distribution field [16][ny][nx] between storage precisions: for the
+// FP32-bulk state the stored deviation g becomes f = F + g on the way to double and
+// f - F on the way back (FieldArgs::Fg).
+cudaError_t launch_convert(const FieldArgs &a, const void *src, int src_prec, void *dst, int dst_prec,
+                           cudaStream_t s);
+// Sums of rho and T over the grid into out2 (for the reference state), using partials.
+cudaError_t launch_field_means(const double *rho, const double *T, size_t n, double *partials,
+                               int nblocks, double *out2, cudaStream_t s);
 
 // Stage kernel selection and launch geometry, shared with the graph builder.
 struct StageLaunch {
     void *func;
     dim3 grid, block;
 };
-StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count);
-cudaError_t launch_stage(const StageLaunch &L, const double *g, const double *base, double *out,
+StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count, int prec);
+cudaError_t launch_stage(const StageLaunch &L, const void *g, const void *base, void *out,
                          const StageArgs &a, unsigned *flag, cudaStream_t s);
+
+// Bytes of one distribution value in storage precision `prec`.
+inline size_t storage_bytes(int prec) { return prec == CDBM_FP32_BULK ? 4 : 8; }
 
 }  // namespace cdbm

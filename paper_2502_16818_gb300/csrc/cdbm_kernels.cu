@@ -1,10 +1,15 @@
-// CDBM kernels (double precision): initial equilibrium, the fused Runge-Kutta
-// stage, macroscopic fields, nonequilibrium moments and conserved sums.
+// CDBM kernels: initial equilibrium, the fused Runge-Kutta stage, macroscopic
+// fields, nonequilibrium moments and conserved sums.  The distribution buffers
+// are stored in double (CDBM_FP64) or single (CDBM_FP32_BULK) precision, selected
+// by the template parameter TS; conserved sums and the equilibrium are always
+// computed in double.
 //
 // Layout: f[16][ny][nx] (velocity plane outermost, x fastest).  One thread owns
 // one cell; a block covers a run of cells along x of one row, so centre loads
-// and stores of a warp are coalesced 256-byte rows and the stencil neighbours
+// and stores of a warp are coalesced rows and the stencil neighbours
 // (x +- 1, 2 and the rows y +- 1, 2) are served from L1/L2.
+#include <type_traits>
+
 #include "cdbm_device.cuh"
 
 namespace cdbm {
@@ -16,13 +21,46 @@ constexpr int kStageThreads = 128;
 #define CDBM_STAGE_MIN_BLOCKS 3   // resident stage blocks per SM the register budget must allow
 #endif
 
+template <typename TS>
+constexpr bool kSingle = std::is_same<TS, float>::value;
+
+// Stage coefficients in the storage precision.
+template <typename TS>
+__device__ __forceinline__ TS a_self_of(const StageArgs &a)
+{
+    if constexpr (kSingle<TS>) return a.a_self_f; else return a.a_self;
+}
+template <typename TS>
+__device__ __forceinline__ TS a_base_of(const StageArgs &a)
+{
+    if constexpr (kSingle<TS>) return a.a_base_f; else return a.a_base;
+}
+template <typename TS>
+__device__ __forceinline__ TS lx_of(const StageArgs &a, int g)
+{
+    if constexpr (kSingle<TS>) return a.lx_f[g]; else return a.lx[g];
+}
+template <typename TS>
+__device__ __forceinline__ TS ly_of(const StageArgs &a, int g)
+{
+    if constexpr (kSingle<TS>) return a.ly_f[g]; else return a.ly[g];
+}
+
+__device__ __forceinline__ double fma_t(double x, double y, double z) { return fma(x, y, z); }
+__device__ __forceinline__ float fma_t(float x, float y, float z) { return fmaf(x, y, z); }
+
+// Stored value of velocity i -> f_i in double (adds the reference F to an FP32 deviation).
+__device__ __forceinline__ double widen(const FieldArgs &, double v, int) { return v; }
+__device__ __forceinline__ double widen(const FieldArgs &a, float v, int i) { return a.Fg[i >> 2] + (double)v; }
+
 // ---------------------------------------------------------------- init (K0)
 
+template <typename TS>
 __global__ void __launch_bounds__(128) init_kernel(const FieldArgs a, const double *__restrict__ rho,
                                                     const double *__restrict__ ux,
                                                     const double *__restrict__ uy,
                                                     const double *__restrict__ T,
-                                                    double *__restrict__ f, unsigned *flag)
+                                                    TS *__restrict__ f, unsigned *flag)
 {
     const size_t P = (size_t)a.nx * a.ny;
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < P;
@@ -38,18 +76,51 @@ __global__ void __launch_bounds__(128) init_kernel(const FieldArgs a, const doub
         if (!(positive_finite(r) && positive_finite(t) && isfinite(u) && isfinite(v)))
             atomicOr(flag, kFlagNonPhys);
 #pragma unroll
-        for (int i = 0; i < kNV; ++i) f[i * P + c] = fe[i];
+        for (int i = 0; i < kNV; ++i) {
+            if constexpr (kSingle<TS>)
+                f[i * P + c] = (float)(fe[i] - a.Fg[i >> 2]);
+            else
+                f[i * P + c] = fe[i];
+        }
     }
+}
+
+// Per-cell macroscopic quantities of the stage: conserved moments (in double),
+// then u, P = rho T and T through the refined reciprocal of rho.
+struct Prim {
+    Cons q;
+    double ux, uy, jyuy, ru2, p, T;
+};
+
+// With kShift, f holds g = f - F and the reference moments rhoF, EF are added.
+template <bool kShift>
+__device__ __forceinline__ Prim primitives(const double f[kNV], const ModelConsts &m, double rhoF,
+                                           double EF, unsigned *flag)
+{
+    Prim s;
+    s.q = conserved(f, m);
+    if (kShift) {
+        s.q.rho += rhoF;
+        s.q.E += EF;
+    }
+    const double r = rcp64(s.q.rho);
+    s.ux = s.q.jx * r;
+    s.uy = s.q.jy * r;
+    s.jyuy = s.q.jy * s.uy;
+    s.ru2 = fma(s.q.jx, s.ux, s.jyuy);
+    s.p = (s.q.E - s.ru2) * m.invK;
+    s.T = s.p * r;
+    if (!(positive_finite(s.q.rho) && positive_finite(s.p))) atomicOr(flag, kFlagNonPhys);
+    return s;
 }
 
 // ------------------------------------------------------------ RK stage (K1/K2)
 
 // out = a_base base + a_self g + gamma h f_eq(g) - sum_r l_r D_r(g) for one cell:
 // macros -> equilibrium -> BGK -> NND transport of all 16 velocities -> update.
-template <bool kBase, bool kFlatY>
-__global__ void __launch_bounds__(kStageThreads, CDBM_STAGE_MIN_BLOCKS) stage_kernel(const double *__restrict__ g,
-                                                              const double *base, double *out,
-                                                              const StageArgs a, unsigned *flag)
+template <typename TS, bool kBase, bool kFlatY>
+__global__ void __launch_bounds__(kStageThreads, CDBM_STAGE_MIN_BLOCKS)
+    stage_kernel(const TS *__restrict__ g, const TS *base, TS *out, const StageArgs a, unsigned *flag)
 {
     const int nx = a.nx, ny = a.ny;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -67,38 +138,35 @@ __global__ void __launch_bounds__(kStageThreads, CDBM_STAGE_MIN_BLOCKS) stage_ke
             rp1 = (size_t)neighbour(y + 1, ny, a.bc_y) * nx + x;
             rp2 = (size_t)neighbour(y + 2, ny, a.bc_y) * nx + x;
         }
+        TS fs[kNV];
         double f[kNV];
 #pragma unroll
-        for (int i = 0; i < kNV; ++i) f[i] = __ldg(g + i * P + c);
-
-        const Cons q = conserved(f, a.m);
-        const double r = rcp64(q.rho);
-        const double ux = q.jx * r, uy = q.jy * r;
-        const double jyuy = q.jy * uy;
-        const double ru2 = fma(q.jx, ux, jyuy);
-        const double p = (q.E - ru2) * a.m.invK;
-        const double T = p * r;
-        if (!(positive_finite(q.rho) && positive_finite(p))) atomicOr(flag, kFlagNonPhys);
+        for (int i = 0; i < kNV; ++i) {
+            fs[i] = __ldg(g + i * P + c);
+            f[i] = (double)fs[i];
+        }
+        const Prim s = primitives<kSingle<TS>>(f, a.m, a.rhoF, a.EF, flag);
         double heq[kNV];
-        equilibrium(a.eq, a.m, q.rho, q.E, q.jx, q.jy, ux, uy, ru2, jyuy, p, T, heq);
+        equilibrium<kSingle<TS>>(a.eq, a.m, s.q.rho, s.q.E, s.q.jx, s.q.jy, s.ux, s.uy, s.ru2, s.jyuy,
+                                 s.p, s.T, heq, a.sF);
 
 #pragma unroll
         for (int i = 0; i < kNV; ++i) {
             const int grp = i >> 2;
-            const double *gp = g + i * P;
-            double o = fma(a.a_self, f[i], heq[i]);
-            if (kBase) o = fma(a.a_base, base[i * P + c], o);
+            const TS *gp = g + i * P;
+            TS o = fma_t(a_self_of<TS>(a), fs[i], (TS)heq[i]);
+            if (kBase) o = fma_t(a_base_of<TS>(a), base[i * P + c], o);
             if (dirx(i) != 0) {
-                const double u2 = __ldg(gp + row + (dirx(i) > 0 ? xm2 : xp2));
-                const double u1 = __ldg(gp + row + (dirx(i) > 0 ? xm1 : xp1));
-                const double d1 = __ldg(gp + row + (dirx(i) > 0 ? xp1 : xm1));
-                o = fma(-a.lx[grp], nnd(u2, u1, f[i], d1), o);
+                const TS u2 = __ldg(gp + row + (dirx(i) > 0 ? xm2 : xp2));
+                const TS u1 = __ldg(gp + row + (dirx(i) > 0 ? xm1 : xp1));
+                const TS d1 = __ldg(gp + row + (dirx(i) > 0 ? xp1 : xm1));
+                o = fma_t(-lx_of<TS>(a, grp), nnd(u2, u1, fs[i], d1), o);
             }
             if (!kFlatY && diry(i) != 0) {
-                const double u2 = __ldg(gp + (diry(i) > 0 ? rm2 : rp2));
-                const double u1 = __ldg(gp + (diry(i) > 0 ? rm1 : rp1));
-                const double d1 = __ldg(gp + (diry(i) > 0 ? rp1 : rm1));
-                o = fma(-a.ly[grp], nnd(u2, u1, f[i], d1), o);
+                const TS u2 = __ldg(gp + (diry(i) > 0 ? rm2 : rp2));
+                const TS u1 = __ldg(gp + (diry(i) > 0 ? rm1 : rp1));
+                const TS d1 = __ldg(gp + (diry(i) > 0 ? rp1 : rm1));
+                o = fma_t(-ly_of<TS>(a, grp), nnd(u2, u1, fs[i], d1), o);
             }
             out[i * P + c] = o;
         }
@@ -109,23 +177,22 @@ __global__ void __launch_bounds__(kStageThreads, CDBM_STAGE_MIN_BLOCKS) stage_ke
 // rows.  A block covers kStageThreads columns and a run of R = ceil(ny / gridDim.y)
 // rows; each thread marches up its column.  For a velocity with y-sign s the
 // upwind-ordered difference U_y = f_y - f_{y-s} and N_y = minmod(U_{y+s}, U_y) give
-// the transport difference U_y + (N_y - N_{y-s}) / 2 (the nnd() expression with
-// a = U_y, b = U_{y-s}... in upwind order); each row computes one new U and one new N
+// the transport difference U_y + (N_y - N_{y-s}) / 2, which is the nnd() expression
+// with a = U_y, b = U_{y-s}, e = U_{y+s}.  Each row computes one new U and one new N
 // per velocity and carries them to the next row in shared memory, so a y-term costs
-// 4 FP64 instructions instead of 6.  The arithmetic is the same as stage_kernel's,
-// operation for operation.
-constexpr int kNY = 12;                    // velocities with a y-component
-__host__ __device__ constexpr int yvel(int k)   // k-th velocity with diry != 0
+// 4 instead of 6 arithmetic instructions, with the same operations as stage_kernel.
+constexpr int kNY = 12;                             // velocities with a y-component
+__host__ __device__ constexpr int yvel(int k)       // k-th velocity with diry != 0
 {
     return k < 2 ? 1 + 2 * k : (k < 6 ? k + 2 : (k < 8 ? 9 + 2 * (k - 6) : k + 4));
 }
 
-template <bool kBase>
-__global__ void __launch_bounds__(kStageThreads, CDBM_STAGE_MIN_BLOCKS) stage_march_kernel(
-    const double *__restrict__ g, const double *base, double *out, const StageArgs a, unsigned *flag)
+template <typename TS, bool kBase>
+__global__ void __launch_bounds__(kStageThreads, CDBM_STAGE_MIN_BLOCKS)
+    stage_march_kernel(const TS *__restrict__ g, const TS *base, TS *out, const StageArgs a, unsigned *flag)
 {
-    __shared__ double carry_u[kNY][kStageThreads];
-    __shared__ double carry_n[kNY][kStageThreads];
+    __shared__ TS carry_u[kNY][kStageThreads];
+    __shared__ TS carry_n[kNY][kStageThreads];
     const int nx = a.nx, ny = a.ny;
     const int tid = threadIdx.x;
     const int x = blockIdx.x * blockDim.x + tid;
@@ -138,7 +205,7 @@ __global__ void __launch_bounds__(kStageThreads, CDBM_STAGE_MIN_BLOCKS) stage_ma
     const int xm2 = neighbour(x - 2, nx, a.bc_x), xm1 = neighbour(x - 1, nx, a.bc_x);
     const int xp1 = neighbour(x + 1, nx, a.bc_x), xp2 = neighbour(x + 2, nx, a.bc_x);
 
-    // prologue: U_{y0} and N_{y0 - s} for s = +1, N_{y0} for s = -1
+    // prologue: U_{y0} and N_{y0 - 1} for s = +1, N_{y0} for s = -1
     {
         const size_t r0 = (size_t)y0 * nx + x;
         const size_t rm1 = (size_t)neighbour(y0 - 1, ny, a.bc_y) * nx + x;
@@ -147,18 +214,18 @@ __global__ void __launch_bounds__(kStageThreads, CDBM_STAGE_MIN_BLOCKS) stage_ma
 #pragma unroll
         for (int k = 0; k < kNY; ++k) {
             const int i = yvel(k);
-            const double *gp = g + i * P;
-            const double f0 = __ldg(gp + r0), fm1 = __ldg(gp + rm1);
+            const TS *gp = g + i * P;
+            const TS f0 = __ldg(gp + r0), fm1 = __ldg(gp + rm1);
             if (diry(i) > 0) {
-                const double u = f0 - fm1;                    // U_{y0}
-                const double um = fm1 - __ldg(gp + rm2);      // U_{y0-1}
+                const TS u = f0 - fm1;                    // U_{y0}
+                const TS um = fm1 - __ldg(gp + rm2);      // U_{y0-1}
                 carry_u[k][tid] = u;
-                carry_n[k][tid] = minmod(u, um);              // N_{y0-1}
+                carry_n[k][tid] = minmod(u, um);          // N_{y0-1}
             } else {
-                const double u = f0 - __ldg(gp + rp1);        // U_{y0}
-                const double um = fm1 - f0;                   // U_{y0-1}
+                const TS u = f0 - __ldg(gp + rp1);        // U_{y0}
+                const TS um = fm1 - f0;                   // U_{y0-1}
                 carry_u[k][tid] = u;
-                carry_n[k][tid] = minmod(um, u);              // N_{y0}
+                carry_n[k][tid] = minmod(um, u);          // N_{y0}
             }
         }
     }
@@ -168,54 +235,52 @@ __global__ void __launch_bounds__(kStageThreads, CDBM_STAGE_MIN_BLOCKS) stage_ma
         const size_t c = row + x;
         const size_t rp1 = (size_t)neighbour(y + 1, ny, a.bc_y) * nx + x;
         const size_t rp2 = (size_t)neighbour(y + 2, ny, a.bc_y) * nx + x;
+        TS fs[kNV];
         double f[kNV];
 #pragma unroll
-        for (int i = 0; i < kNV; ++i) f[i] = __ldg(g + i * P + c);
+        for (int i = 0; i < kNV; ++i) {
+            fs[i] = __ldg(g + i * P + c);
+            f[i] = (double)fs[i];
+        }
+        const Prim s = primitives<kSingle<TS>>(f, a.m, a.rhoF, a.EF, flag);
+        double heq[kNV];
+        equilibrium<kSingle<TS>>(a.eq, a.m, s.q.rho, s.q.E, s.q.jx, s.q.jy, s.ux, s.uy, s.ru2, s.jyuy,
+                                 s.p, s.T, heq, a.sF);
 
-        const Cons q = conserved(f, a.m);
-        const double r = rcp64(q.rho);
-        const double ux = q.jx * r, uy = q.jy * r;
-        const double jyuy = q.jy * uy;
-        const double ru2 = fma(q.jx, ux, jyuy);
-        const double p = (q.E - ru2) * a.m.invK;
-        const double T = p * r;
-        if (!(positive_finite(q.rho) && positive_finite(p))) atomicOr(flag, kFlagNonPhys);
-        double o[kNV];
-        equilibrium(a.eq, a.m, q.rho, q.E, q.jx, q.jy, ux, uy, ru2, jyuy, p, T, o);
-
+        TS o[kNV];
 #pragma unroll
         for (int i = 0; i < kNV; ++i) {
-            o[i] = fma(a.a_self, f[i], o[i]);
-            if (kBase) o[i] = fma(a.a_base, base[i * P + c], o[i]);
+            o[i] = fma_t(a_self_of<TS>(a), fs[i], (TS)heq[i]);
+            if (kBase) o[i] = fma_t(a_base_of<TS>(a), base[i * P + c], o[i]);
             if (dirx(i) != 0) {
-                const double *gp = g + i * P + row;
-                const double u2 = __ldg(gp + (dirx(i) > 0 ? xm2 : xp2));
-                const double u1 = __ldg(gp + (dirx(i) > 0 ? xm1 : xp1));
-                const double d1 = __ldg(gp + (dirx(i) > 0 ? xp1 : xm1));
-                o[i] = fma(-a.lx[i >> 2], nnd(u2, u1, f[i], d1), o[i]);
+                const TS *gp = g + i * P + row;
+                const TS u2 = __ldg(gp + (dirx(i) > 0 ? xm2 : xp2));
+                const TS u1 = __ldg(gp + (dirx(i) > 0 ? xm1 : xp1));
+                const TS d1 = __ldg(gp + (dirx(i) > 0 ? xp1 : xm1));
+                o[i] = fma_t(-lx_of<TS>(a, i >> 2), nnd(u2, u1, fs[i], d1), o[i]);
             }
         }
 #pragma unroll
         for (int k = 0; k < kNY; ++k) {
             const int i = yvel(k);
-            const double *gp = g + i * P;
-            const double u = carry_u[k][tid];
-            const double n = carry_n[k][tid];
-            double t;
+            const TS *gp = g + i * P;
+            const TS u = carry_u[k][tid];
+            const TS n = carry_n[k][tid];
+            TS t;
             if (diry(i) > 0) {
-                const double un = __ldg(gp + rp1) - f[i];     // U_{y+1}
-                const double nn = minmod(un, u);              // N_y
-                t = nn - n;                                   // N_y - N_{y-1}
+                const TS un = __ldg(gp + rp1) - fs[i];                  // U_{y+1}
+                const TS nn = minmod(un, u);                            // N_y
+                t = nn - n;                                             // N_y - N_{y-1}
                 carry_u[k][tid] = un;
                 carry_n[k][tid] = nn;
             } else {
-                const double un = __ldg(gp + rp1) - __ldg(gp + rp2);   // U_{y+1}
-                const double nn = minmod(u, un);                        // N_{y+1}
+                const TS un = __ldg(gp + rp1) - __ldg(gp + rp2);        // U_{y+1}
+                const TS nn = minmod(u, un);                            // N_{y+1}
                 t = n - nn;                                             // N_y - N_{y+1}
                 carry_u[k][tid] = un;
                 carry_n[k][tid] = nn;
             }
-            o[i] = fma(-a.ly[i >> 2], fma(0.5, t, u), o[i]);
+            o[i] = fma_t(-ly_of<TS>(a, i >> 2), fma_t((TS)0.5, t, u), o[i]);
         }
 #pragma unroll
         for (int i = 0; i < kNV; ++i) out[i * P + c] = o[i];
@@ -224,7 +289,8 @@ __global__ void __launch_bounds__(kStageThreads, CDBM_STAGE_MIN_BLOCKS) stage_ma
 
 // ------------------------------------------------------------ macros (K3)
 
-__global__ void __launch_bounds__(128) macros_kernel(const FieldArgs a, const double *__restrict__ f,
+template <typename TS>
+__global__ void __launch_bounds__(128) macros_kernel(const FieldArgs a, const TS *__restrict__ f,
                                                       double *rho, double *ux, double *uy, double *T)
 {
     const size_t P = (size_t)a.nx * a.ny;
@@ -232,7 +298,7 @@ __global__ void __launch_bounds__(128) macros_kernel(const FieldArgs a, const do
          c += (size_t)gridDim.x * blockDim.x) {
         double fc[kNV];
 #pragma unroll
-        for (int i = 0; i < kNV; ++i) fc[i] = f[i * P + c];
+        for (int i = 0; i < kNV; ++i) fc[i] = widen(a, f[i * P + c], i);
         const Cons q = conserved(fc, a.m);
         const double u = q.jx / q.rho, v = q.jy / q.rho;
         const double ru2 = fma(q.jx, u, q.jy * v);
@@ -246,7 +312,8 @@ __global__ void __launch_bounds__(128) macros_kernel(const FieldArgs a, const do
 // ------------------------------------------------------------ TNE (K4)
 
 // Rows 5..16 of M(u) (Eq. 6) applied to f - f_eq: Delta* of Eqs. (8)-(11).
-__global__ void __launch_bounds__(128) tne_kernel(const FieldArgs a, const double *__restrict__ f,
+template <typename TS>
+__global__ void __launch_bounds__(128) tne_kernel(const FieldArgs a, const TS *__restrict__ f,
                                                    double *__restrict__ out)
 {
     const size_t P = (size_t)a.nx * a.ny;
@@ -254,7 +321,7 @@ __global__ void __launch_bounds__(128) tne_kernel(const FieldArgs a, const doubl
          c += (size_t)gridDim.x * blockDim.x) {
         double fc[kNV];
 #pragma unroll
-        for (int i = 0; i < kNV; ++i) fc[i] = f[i * P + c];
+        for (int i = 0; i < kNV; ++i) fc[i] = widen(a, f[i * P + c], i);
         const Cons q = conserved(fc, a.m);
         const double u = q.jx / q.rho, v = q.jy / q.rho;
         const double jyuy = q.jy * v;
@@ -297,8 +364,9 @@ constexpr int kSumThreads = 256;
 
 // Block b reduces cells [b*chunk, (b+1)*chunk) in a fixed order and writes its
 // four partial sums; the order depends only on the grid size and nblocks.
+template <typename TS>
 __global__ void __launch_bounds__(kSumThreads) sums_partial_kernel(const FieldArgs a,
-                                                                   const double *__restrict__ f,
+                                                                   const TS *__restrict__ f,
                                                                    double *__restrict__ partials)
 {
     __shared__ double sh[4][kSumThreads];
@@ -310,7 +378,7 @@ __global__ void __launch_bounds__(kSumThreads) sums_partial_kernel(const FieldAr
     for (size_t c = lo + threadIdx.x; c < hi; c += kSumThreads) {
         double fc[kNV];
 #pragma unroll
-        for (int i = 0; i < kNV; ++i) fc[i] = f[i * P + c];
+        for (int i = 0; i < kNV; ++i) fc[i] = widen(a, f[i * P + c], i);
         const Cons q = conserved(fc, a.m);
         s[0] += q.rho;
         s[1] += q.jx;
@@ -337,43 +405,137 @@ __global__ void sums_final_kernel(const double *__restrict__ partials, int nbloc
     }
 }
 
+// ------------------------------------------------------------ conversion
+
+// FP32-bulk deviation g <-> f = F + g for a whole [16][plane] field.
+__global__ void __launch_bounds__(256) widen_kernel(const FieldArgs a, const float *__restrict__ in,
+                                                     double *__restrict__ out, size_t plane)
+{
+    const size_t n = kNV * plane;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        out[k] = a.Fg[(int)(k / plane) >> 2] + (double)in[k];
+}
+
+__global__ void __launch_bounds__(256) narrow_kernel(const FieldArgs a, const double *__restrict__ in,
+                                                      float *__restrict__ out, size_t plane)
+{
+    const size_t n = kNV * plane;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        out[k] = (float)(in[k] - a.Fg[(int)(k / plane) >> 2]);
+}
+
+// Block partial sums of rho and T (fixed order), then one block adds the partials.
+__global__ void __launch_bounds__(kSumThreads) means_partial_kernel(const double *__restrict__ rho,
+                                                                    const double *__restrict__ T, size_t n,
+                                                                    double *__restrict__ partials)
+{
+    __shared__ double sh[2][kSumThreads];
+    const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const size_t lo = blockIdx.x * chunk;
+    const size_t hi = lo + chunk < n ? lo + chunk : n;
+    double s0 = 0.0, s1 = 0.0;
+    for (size_t c = lo + threadIdx.x; c < hi; c += kSumThreads) {
+        s0 += rho[c];
+        s1 += T[c];
+    }
+    sh[0][threadIdx.x] = s0;
+    sh[1][threadIdx.x] = s1;
+    __syncthreads();
+    for (int w = kSumThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 2) partials[blockIdx.x * 4 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
 unsigned grid_for(size_t cells, int threads)
 {
     size_t b = (cells + threads - 1) / threads;
     return (unsigned)(b < 1 ? 1 : (b > 1048576 ? 1048576 : b));
 }
 
+template <typename TS>
+void *stage_func(bool march, bool with_base, bool flat)
+{
+    if (march)
+        return with_base ? (void *)stage_march_kernel<TS, true> : (void *)stage_march_kernel<TS, false>;
+    if (with_base)
+        return flat ? (void *)stage_kernel<TS, true, true> : (void *)stage_kernel<TS, true, false>;
+    return flat ? (void *)stage_kernel<TS, false, true> : (void *)stage_kernel<TS, false, false>;
+}
+
 }  // namespace
 
 cudaError_t launch_init(const FieldArgs &a, const double *rho, const double *ux, const double *uy,
-                        const double *T, double *f, unsigned *flag, cudaStream_t s)
+                        const double *T, void *f, int prec, unsigned *flag, cudaStream_t s)
 {
-    init_kernel<<<grid_for((size_t)a.nx * a.ny, 128), 128, 0, s>>>(a, rho, ux, uy, T, f, flag);
+    const unsigned nb = grid_for((size_t)a.nx * a.ny, 128);
+    if (prec == CDBM_FP32_BULK)
+        init_kernel<float><<<nb, 128, 0, s>>>(a, rho, ux, uy, T, (float *)f, flag);
+    else
+        init_kernel<double><<<nb, 128, 0, s>>>(a, rho, ux, uy, T, (double *)f, flag);
     return cudaGetLastError();
 }
 
-cudaError_t launch_macros(const FieldArgs &a, const double *f, double *rho, double *ux, double *uy,
-                          double *T, cudaStream_t s)
+cudaError_t launch_macros(const FieldArgs &a, const void *f, int prec, double *rho, double *ux,
+                          double *uy, double *T, cudaStream_t s)
 {
-    macros_kernel<<<grid_for((size_t)a.nx * a.ny, 128), 128, 0, s>>>(a, f, rho, ux, uy, T);
+    const unsigned nb = grid_for((size_t)a.nx * a.ny, 128);
+    if (prec == CDBM_FP32_BULK)
+        macros_kernel<float><<<nb, 128, 0, s>>>(a, (const float *)f, rho, ux, uy, T);
+    else
+        macros_kernel<double><<<nb, 128, 0, s>>>(a, (const double *)f, rho, ux, uy, T);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tne(const FieldArgs &a, const double *f, double *out, cudaStream_t s)
+cudaError_t launch_tne(const FieldArgs &a, const void *f, int prec, double *out, cudaStream_t s)
 {
-    tne_kernel<<<grid_for((size_t)a.nx * a.ny, 128), 128, 0, s>>>(a, f, out);
+    const unsigned nb = grid_for((size_t)a.nx * a.ny, 128);
+    if (prec == CDBM_FP32_BULK)
+        tne_kernel<float><<<nb, 128, 0, s>>>(a, (const float *)f, out);
+    else
+        tne_kernel<double><<<nb, 128, 0, s>>>(a, (const double *)f, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sums(const FieldArgs &a, const double *f, double *partials, int nblocks,
+cudaError_t launch_sums(const FieldArgs &a, const void *f, int prec, double *partials, int nblocks,
                         double *out4, cudaStream_t s)
 {
-    sums_partial_kernel<<<nblocks, kSumThreads, 0, s>>>(a, f, partials);
+    if (prec == CDBM_FP32_BULK)
+        sums_partial_kernel<float><<<nblocks, kSumThreads, 0, s>>>(a, (const float *)f, partials);
+    else
+        sums_partial_kernel<double><<<nblocks, kSumThreads, 0, s>>>(a, (const double *)f, partials);
     sums_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, out4);
     return cudaGetLastError();
 }
 
-StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count)
+cudaError_t launch_convert(const FieldArgs &a, const void *src, int src_prec, void *dst, int dst_prec,
+                           cudaStream_t s)
+{
+    const size_t plane = (size_t)a.nx * a.ny;
+    const unsigned nb = grid_for(kNV * plane, 256);
+    const bool si = src_prec == CDBM_FP32_BULK, so = dst_prec == CDBM_FP32_BULK;
+    if (si && !so)
+        widen_kernel<<<nb, 256, 0, s>>>(a, (const float *)src, (double *)dst, plane);
+    else if (!si && so)
+        narrow_kernel<<<nb, 256, 0, s>>>(a, (const double *)src, (float *)dst, plane);
+    else
+        return cudaMemcpyAsync(dst, src, kNV * plane * storage_bytes(src_prec), cudaMemcpyDefault, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_means(const double *rho, const double *T, size_t n, double *partials,
+                               int nblocks, double *out2, cudaStream_t s)
+{
+    means_partial_kernel<<<nblocks, kSumThreads, 0, s>>>(rho, T, n, partials);
+    sums_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, out2);
+    return cudaGetLastError();
+}
+
+StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count, int prec)
 {
     StageLaunch L;
     const bool flat = (a.ny == 1);
@@ -384,17 +546,15 @@ StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count
     const size_t wave = (size_t)sm_count * CDBM_STAGE_MIN_BLOCKS;
     int R = 8;
     while (R < 32 && (size_t)xblocks * ((a.ny + 2 * R - 1) / (2 * R)) >= 8 * wave) R *= 2;
-    if (!flat && a.ny >= 16 && (size_t)xblocks * ((a.ny + 7) / 8) >= 2 * wave) {
-        L.func = with_base ? (void *)stage_march_kernel<true> : (void *)stage_march_kernel<false>;
+    const bool march = !flat && a.ny >= 16 && (size_t)xblocks * ((a.ny + 7) / 8) >= 2 * wave;
+    L.func = prec == CDBM_FP32_BULK ? stage_func<float>(march, with_base, flat)
+                                    : stage_func<double>(march, with_base, flat);
+    if (march) {
         L.block = dim3(kStageThreads, 1, 1);
         const unsigned yblocks = (unsigned)((a.ny + R - 1) / R);
         L.grid = dim3(xblocks, yblocks < 65535 ? yblocks : 65535, 1);
         return L;
     }
-    if (with_base)
-        L.func = flat ? (void *)stage_kernel<true, true> : (void *)stage_kernel<true, false>;
-    else
-        L.func = flat ? (void *)stage_kernel<false, true> : (void *)stage_kernel<false, false>;
     // Small grids: narrower blocks so that more SMs share the cells.
     int threads = kStageThreads;
     while (threads > 32 && cells < (size_t)sm_count * threads * 2) threads >>= 1;
@@ -403,7 +563,7 @@ StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count
     return L;
 }
 
-cudaError_t launch_stage(const StageLaunch &L, const double *g, const double *base, double *out,
+cudaError_t launch_stage(const StageLaunch &L, const void *g, const void *base, void *out,
                          const StageArgs &a, unsigned *flag, cudaStream_t s)
 {
     void *args[] = {(void *)&g, (void *)&base, (void *)&out, (void *)&a, (void *)&flag};

@@ -135,11 +135,17 @@ extern "C" cdbm_status cdbm_step_noalloc(const cdbm_grid *grid, const cdbm_vset 
             a[s].lx[g] = gamma[s] * dt * mc.c[g] / grid->dx;
             a[s].ly[g] = gamma[s] * dt * mc.c[g] / grid->dy;
         }
+        a[s].a_base_f = (float)a[s].a_base;
+        a[s].a_self_f = (float)a[s].a_self;
+        for (int g = 0; g < 4; ++g) {
+            a[s].lx_f[g] = (float)a[s].lx[g];
+            a[s].ly_f[g] = (float)a[s].ly[g];
+        }
         a[s].nx = grid->nx;
         a[s].ny = grid->ny;
         a[s].bc_x = grid->bc_x;
         a[s].bc_y = grid->bc_y;
-        L[s] = stage_launch_config(a[s], s == 1, sm_count);
+        L[s] = stage_launch_config(a[s], s == 1, sm_count, CDBM_FP64);
     }
 
     // The flag keeps the previous call's value: clear it first.
