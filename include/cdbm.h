@@ -181,6 +181,58 @@ const char *cdbm_last_error(const cdbm_ctx *ctx);
 /* Releases the context and its device memory (stream-ordered).  NULL is a no-op. */
 void cdbm_destroy(cdbm_ctx *ctx);
 
+/* ------------------------------------------------------------------------------
+ * Batched ensembles of 1-D tubes.  Each tube is an independent Ny = 1 run of Eq. (1)
+ * with zero-gradient ends (a shock tube), with its own number of cells, cell size,
+ * I and initial state; all tubes share the velocity set, tau and dt.  The tubes are
+ * concatenated along x: a batch field is [total_cells] (tube t at cells
+ * offset_t .. offset_t + nx_t - 1, offsets in tube order); the state is
+ * [16][total_cells].  One persistent kernel advances every tube through all
+ * requested steps; a block owns a fixed set of whole tubes, so blocks never wait on
+ * one another (block barriers only, between Runge-Kutta stages).  The two-stage TVD
+ * scheme is used.  Precision: CDBM_FP64 or CDBM_FP32_BULK (per-tube reference F =
+ * f_eq of the tube's mean rho and T).
+ * ---------------------------------------------------------------------------- */
+typedef struct cdbm_batch cdbm_batch;
+
+/* Validates and builds a batch of ntubes tubes: nx[t] >= 1 cells of size dx[t] > 0
+ * and I[t] >= 0 (at most 4 distinct values of I); host arrays, copied.  Errors as
+ * cdbm_create (CFL checked per tube along x).  The initial tile is 128 threads per
+ * block and 3 blocks per SM. */
+cdbm_status cdbm_batch_create(int ntubes, const int *nx, const double *dx, const double *I,
+                              const cdbm_vset *vset, double tau, double dt, int precision,
+                              void *cuda_stream, const cdbm_allocator *allocator, cdbm_batch **out);
+
+/* f = f_eq(rho, u, T) in every cell of every tube; fields [total_cells], host or
+ * device.  Synchronous. */
+cdbm_status cdbm_batch_init(cdbm_batch *b, const double *rho, const double *ux, const double *uy,
+                            const double *T);
+
+/* Advances every tube by nsteps >= 0 steps: one persistent launch, replayed from a
+ * CUDA graph.  Asynchronous; cdbm_batch_sync reports a non-physical state. */
+cdbm_status cdbm_batch_step(cdbm_batch *b, int nsteps);
+
+/* Times the candidate tiles (64/128/256 threads per block x 1-4 blocks per SM, each
+ * with its own longest-first partition of the tubes) over trial_steps steps, keeps
+ * the fastest and reports it.  The state is saved before and restored after the
+ * trials, and results do not depend on the tile. */
+cdbm_status cdbm_batch_autotune(cdbm_batch *b, int trial_steps, int *threads, int *blocks_per_sm);
+
+/* Sets the tile explicitly (threads 64, 128 or 256; blocks_per_sm 1..16). */
+cdbm_status cdbm_batch_set_tile(cdbm_batch *b, int threads, int blocks_per_sm);
+
+/* rho, u_x, u_y, T of every cell ([total_cells] each, host or device, NULL skips).
+ * Synchronous. */
+cdbm_status cdbm_batch_macros(cdbm_batch *b, double *rho, double *ux, double *uy, double *T);
+
+/* Total cells and the current tile (threads per block, number of blocks). */
+cdbm_status cdbm_batch_info(const cdbm_batch *b, long long *total_cells, int *threads, int *blocks);
+
+/* Waits for the batch's stream; reports a sticky error or CDBM_ENONPHYS. */
+cdbm_status cdbm_batch_sync(cdbm_batch *b);
+const char *cdbm_batch_last_error(const cdbm_batch *b);
+void cdbm_batch_destroy(cdbm_batch *b);
+
 /* Largest grid (nx * ny cells) that cdbm_step_noalloc accepts. */
 #define CDBM_NOALLOC_MAX_CELLS 32768
 

@@ -5,7 +5,7 @@ The compute path is the CUDA library ``_build/libcdbm.so`` (C ABI in
 wrapper that takes device memory and streams from PyTorch.  ``workloads`` holds
 the seeded initial conditions of the paper's test problems.
 """
-from .cdbm import (CdbmError, Solver, CDBM_BC_PERIODIC, CDBM_BC_ZEROGRAD, CDBM_FP64,  # noqa: F401
+from .cdbm import (BatchSolver, CdbmError, Solver, CDBM_BC_PERIODIC, CDBM_BC_ZEROGRAD, CDBM_FP64,  # noqa: F401
                    CDBM_FP32_BULK, CDBM_RK2_MIDPOINT, CDBM_RK2_TVD)
 from . import workloads  # noqa: F401
 

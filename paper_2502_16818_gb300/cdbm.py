@@ -26,7 +26,10 @@ CDBM_RK2_TVD, CDBM_RK2_MIDPOINT = 0, 1
 #: every entry point declared in include/cdbm.h
 EXPORTS = ("cdbm_create", "cdbm_set_rk", "cdbm_init", "cdbm_step", "cdbm_macros", "cdbm_tne",
            "cdbm_conserved_sums", "cdbm_get_state", "cdbm_set_state", "cdbm_state_ptr", "cdbm_time",
-           "cdbm_sync", "cdbm_last_error", "cdbm_destroy", "cdbm_step_noalloc")
+           "cdbm_sync", "cdbm_last_error", "cdbm_destroy", "cdbm_step_noalloc",
+           "cdbm_batch_create", "cdbm_batch_init", "cdbm_batch_step", "cdbm_batch_autotune",
+           "cdbm_batch_set_tile", "cdbm_batch_macros", "cdbm_batch_info", "cdbm_batch_sync",
+           "cdbm_batch_last_error", "cdbm_batch_destroy")
 CDBM_NOALLOC_MAX_CELLS = 32768
 
 
@@ -91,6 +94,20 @@ def load(path: str | None = None):
         "cdbm_destroy": ([ctx], None),
         "cdbm_step_noalloc": ([ctypes.POINTER(cdbm_grid), ctypes.POINTER(cdbm_vset), ctypes.c_double,
                                ctypes.c_double, ctypes.c_double, _vp, ctypes.c_int, _vp], ctypes.c_int),
+        "cdbm_batch_create": ([ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(cdbm_vset), ctypes.c_double,
+                               ctypes.c_double, ctypes.c_int, _vp, ctypes.POINTER(cdbm_allocator),
+                               ctypes.POINTER(ctx)], ctypes.c_int),
+        "cdbm_batch_init": ([ctx, _vp, _vp, _vp, _vp], ctypes.c_int),
+        "cdbm_batch_step": ([ctx, ctypes.c_int], ctypes.c_int),
+        "cdbm_batch_autotune": ([ctx, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "cdbm_batch_set_tile": ([ctx, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "cdbm_batch_macros": ([ctx, _vp, _vp, _vp, _vp], ctypes.c_int),
+        "cdbm_batch_info": ([ctx, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int),
+                             ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "cdbm_batch_sync": ([ctx], ctypes.c_int),
+        "cdbm_batch_last_error": ([ctx], ctypes.c_char_p),
+        "cdbm_batch_destroy": ([ctx], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -196,6 +213,73 @@ def cdbm_step_noalloc(grid: cdbm_grid, vset: cdbm_vset, I, tau, dt, f, nsteps, s
     st = lib.cdbm_step_noalloc(ctypes.byref(grid), ctypes.byref(vset), float(I), float(tau),
                                float(dt), ctypes.c_void_p(f), int(nsteps), ctypes.c_void_p(stream))
     _check(lib, None, st)
+
+
+def _bcheck(lib, b, status):
+    if status != CDBM_OK:
+        raise CdbmError(status, lib.cdbm_batch_last_error(b).decode())
+
+
+def cdbm_batch_create(nx, dx, I, vset: cdbm_vset, tau, dt, precision=CDBM_FP64, stream=0,
+                      allocator: cdbm_allocator | None = None):
+    lib = load()
+    n = len(nx)
+    nx_a = np.ascontiguousarray(nx, dtype=np.int32)
+    dx_a = np.ascontiguousarray(dx, dtype=np.float64)
+    I_a = np.ascontiguousarray(I, dtype=np.float64)
+    out = ctypes.c_void_p()
+    st = lib.cdbm_batch_create(n, nx_a.ctypes.data, dx_a.ctypes.data, I_a.ctypes.data, ctypes.byref(vset),
+                               float(tau), float(dt), int(precision), ctypes.c_void_p(stream),
+                               ctypes.byref(allocator) if allocator is not None else None, ctypes.byref(out))
+    _bcheck(lib, None, st)
+    return out
+
+
+def cdbm_batch_init(b, rho, ux, uy, T):
+    lib = load()
+    _bcheck(lib, b, lib.cdbm_batch_init(b, rho, ux, uy, T))
+
+
+def cdbm_batch_step(b, nsteps):
+    lib = load()
+    _bcheck(lib, b, lib.cdbm_batch_step(b, int(nsteps)))
+
+
+def cdbm_batch_autotune(b, trial_steps):
+    lib = load()
+    t, k = ctypes.c_int(), ctypes.c_int()
+    _bcheck(lib, b, lib.cdbm_batch_autotune(b, int(trial_steps), ctypes.byref(t), ctypes.byref(k)))
+    return t.value, k.value
+
+
+def cdbm_batch_set_tile(b, threads, blocks_per_sm):
+    lib = load()
+    _bcheck(lib, b, lib.cdbm_batch_set_tile(b, int(threads), int(blocks_per_sm)))
+
+
+def cdbm_batch_macros(b, rho, ux, uy, T):
+    lib = load()
+    _bcheck(lib, b, lib.cdbm_batch_macros(b, rho, ux, uy, T))
+
+
+def cdbm_batch_info(b):
+    lib = load()
+    n, t, k = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int()
+    _bcheck(lib, b, lib.cdbm_batch_info(b, ctypes.byref(n), ctypes.byref(t), ctypes.byref(k)))
+    return n.value, t.value, k.value
+
+
+def cdbm_batch_sync(b):
+    lib = load()
+    _bcheck(lib, b, lib.cdbm_batch_sync(b))
+
+
+def cdbm_batch_last_error(b) -> str:
+    return load().cdbm_batch_last_error(b).decode()
+
+
+def cdbm_batch_destroy(b):
+    load().cdbm_batch_destroy(b)
 
 
 # ------------------------------------------------------------------ Solver
@@ -309,6 +393,82 @@ class Solver:
         if getattr(self, "ctx", None):
             cdbm_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchSolver:
+    """An ensemble of independent 1-D tubes advanced by one persistent kernel
+    (cdbm_batch_*).  ``tubes`` is a list of workloads with ny == 1 sharing the
+    velocity set, tau and dt (for example ``workloads.ensemble_tube``)."""
+
+    def __init__(self, tubes, precision=CDBM_FP64, stream=None):
+        import torch
+        self._torch = torch
+        self.device = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        w0 = tubes[0]
+        for w in tubes:
+            assert w.ny == 1 and w.vg == w0.vg and w.eg == w0.eg and w.dt == w0.dt and w.tau == w0.tau
+        self.nx = [w.nx for w in tubes]
+        self.offsets = np.concatenate([[0], np.cumsum(self.nx)])
+        dev = self.device
+
+        def _alloc(nbytes, strm, user):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev, strm or 0)
+            except Exception:
+                return None
+
+        def _free(ptr, nbytes, strm, user):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._alloc_cb = ALLOC_FN(_alloc)
+        self._free_cb = FREE_FN(_free)
+        self._allocator = cdbm_allocator(self._alloc_cb, self._free_cb, None)
+        vset = cdbm_vset((ctypes.c_double * 4)(*w0.vg), (ctypes.c_double * 4)(*w0.eg))
+        self.b = cdbm_batch_create(self.nx, [w.dx for w in tubes], [w.I for w in tubes], vset, w0.tau,
+                                   w0.dt, precision, self.stream.cuda_stream, self._allocator)
+        self.total = int(self.offsets[-1])
+
+    def init(self, tubes):
+        fields = [np.ascontiguousarray(np.concatenate([getattr(w, k).reshape(-1) for w in tubes]))
+                  for k in ("rho", "ux", "uy", "T")]
+        cdbm_batch_init(self.b, *(a.ctypes.data for a in fields))
+
+    def step(self, nsteps=1):
+        cdbm_batch_step(self.b, nsteps)
+
+    def autotune(self, trial_steps=5):
+        return cdbm_batch_autotune(self.b, trial_steps)
+
+    def set_tile(self, threads, blocks_per_sm):
+        cdbm_batch_set_tile(self.b, threads, blocks_per_sm)
+
+    def macros(self):
+        """(rho, ux, uy, T) as concatenated float64 numpy arrays."""
+        out = [np.zeros(self.total) for _ in range(4)]
+        cdbm_batch_macros(self.b, *(a.ctypes.data for a in out))
+        return tuple(out)
+
+    def tube(self, arrays, t):
+        lo, hi = self.offsets[t], self.offsets[t + 1]
+        return tuple(a[lo:hi] for a in arrays)
+
+    def info(self):
+        return cdbm_batch_info(self.b)
+
+    def sync(self):
+        cdbm_batch_sync(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            cdbm_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

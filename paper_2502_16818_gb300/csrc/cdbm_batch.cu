@@ -1,0 +1,716 @@
+// Batched ensemble of independent 1-D tubes (Ny = 1, zero-gradient ends), each with
+// its own length, cell size, I and initial state, advanced together by one
+// persistent kernel.
+//
+// Layout: the tubes are concatenated along x into one [16][P] field (P = total
+// cells); tube t owns cells [offset_t, offset_t + nx_t).  A block owns a fixed list
+// of whole tubes (a longest-first partition of their cost) and advances each of
+// them through all requested steps before moving on, so a tube's two buffers stay
+// in L2 for the whole run and the only synchronisation is the block barrier
+// between Runge-Kutta stages: tubes never exchange data, so blocks never wait on
+// one another.  The tile shape -- threads per block and blocks per SM, which set
+// how the tubes are partitioned -- is picked by cdbm_batch_autotune by timing the
+// candidates on the batch itself.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "cdbm_device.cuh"
+#include "cdbm_internal.h"
+
+using namespace cdbm;
+
+namespace {
+
+constexpr int kMaxClasses = 4;        // distinct values of I in one batch
+
+struct TubeInfo {
+    long long offset;                 // first cell of the tube in the [16][P] planes
+    int nx;
+    int cls;                          // index of the tube's I in BatchArgs::cls
+    double lx[2][4];                  // per stage: gamma dt c_g / dx_t
+    float lx_f[2][4];
+    double sF[2][4];                  // per stage: gamma h F_g (FP32-bulk reference)
+    double Fg[4];                     // reference equilibrium per group
+    double rhoF, EF;                  // its conserved moments
+};
+
+struct ClassConsts {
+    EqBlocks eq[2];                   // per stage, scaled by gamma h
+    EqBlocks unit;                    // unscaled (initialisation, macros)
+    ModelConsts m;
+};
+
+struct BatchArgs {
+    ClassConsts cls[kMaxClasses];
+    double a_self[2], a_base[2];
+    float a_self_f[2], a_base_f[2];
+    long long P;                      // total cells: stride between velocity planes
+};
+
+template <typename TS>
+__device__ __forceinline__ TS pick(double d, float f)
+{
+    if constexpr (kSingle<TS>) return f; else return d;
+}
+
+// One Runge-Kutta stage over the nx cells of one tube by the calling block.  g, base
+// and out point at the tube's first cell; planes are P apart.  The arithmetic per
+// cell is the flat (Ny = 1) stage of the single-grid kernels.  Plain loads: the
+// buffers are written inside this kernel, so the read-only path may not be used.
+template <typename TS, bool kBase>
+__device__ __forceinline__ void tube_stage(const TS *g, const TS *base, TS *out, long long P, int nx,
+                                           const EqBlocks &eq, const ModelConsts &m, TS a_self,
+                                           TS a_base, const double *lx, const float *lx_f,
+                                           const double *sF, double rhoF, double EF, unsigned *flag)
+{
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+        const int xm2 = x >= 2 ? x - 2 : 0, xm1 = x >= 1 ? x - 1 : 0;
+        const int xp1 = x + 1 < nx ? x + 1 : nx - 1, xp2 = x + 2 < nx ? x + 2 : nx - 1;
+        TS fs[kNV];
+        double f[kNV];
+#pragma unroll
+        for (int i = 0; i < kNV; ++i) {
+            fs[i] = g[i * P + x];
+            f[i] = (double)fs[i];
+        }
+        const Prim s = primitives<kSingle<TS>>(f, m, rhoF, EF, flag);
+        double heq[kNV];
+        equilibrium<kSingle<TS>>(eq, m, s.q.rho, s.q.E, s.q.jx, s.q.jy, s.ux, s.uy, s.ru2, s.jyuy, s.p,
+                                 s.T, heq, sF);
+#pragma unroll
+        for (int i = 0; i < kNV; ++i) {
+            TS o = fma_t(a_self, fs[i], (TS)heq[i]);
+            if (kBase) o = fma_t(a_base, base[i * P + x], o);
+            if (dirx(i) != 0) {
+                const TS *gp = g + i * P;
+                const TS u2 = gp[dirx(i) > 0 ? xm2 : xp2];
+                const TS u1 = gp[dirx(i) > 0 ? xm1 : xp1];
+                const TS d1 = gp[dirx(i) > 0 ? xp1 : xm1];
+                o = fma_t(-pick<TS>(lx[i >> 2], lx_f[i >> 2]), nnd(u2, u1, fs[i], d1), o);
+            }
+            out[i * P + x] = o;
+        }
+    }
+}
+
+template <typename TS, int kThreads>
+__global__ void __launch_bounds__(kThreads, (384 / kThreads > 0 ? 384 / kThreads : 1)) batch_kernel(TS *f, TS *f1, const TubeInfo *tubes,
+                                                         const int *work, const int *work_off, int nsteps,
+                                                         const BatchArgs a, unsigned *flag)
+{
+    const TS as0 = pick<TS>(a.a_self[0], a.a_self_f[0]), as1 = pick<TS>(a.a_self[1], a.a_self_f[1]);
+    const TS ab0 = pick<TS>(a.a_base[0], a.a_base_f[0]), ab1 = pick<TS>(a.a_base[1], a.a_base_f[1]);
+    for (int w = work_off[blockIdx.x]; w < work_off[blockIdx.x + 1]; ++w) {
+        const TubeInfo &t = tubes[work[w]];
+        const ClassConsts &C = a.cls[t.cls];
+        TS *ft = f + t.offset;
+        TS *f1t = f1 + t.offset;
+        for (int s = 0; s < nsteps; ++s) {
+            tube_stage<TS, false>(ft, nullptr, f1t, a.P, t.nx, C.eq[0], C.m, as0, ab0, t.lx[0], t.lx_f[0],
+                                  t.sF[0], t.rhoF, t.EF, flag);
+            __syncthreads();
+            tube_stage<TS, true>(f1t, ft, ft, a.P, t.nx, C.eq[1], C.m, as1, ab1, t.lx[1], t.lx_f[1],
+                                 t.sF[1], t.rhoF, t.EF, flag);
+            __syncthreads();
+        }
+    }
+}
+
+// Tube of a global cell index (offsets ascending, ntubes + 1 entries with the total last).
+__device__ __forceinline__ int tube_of(const long long *offs, int ntubes, long long c)
+{
+    int lo = 0, hi = ntubes;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (offs[mid] <= c) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <typename TS>
+__global__ void __launch_bounds__(128) batch_init_kernel(const BatchArgs a, const TubeInfo *tubes,
+                                                          const long long *offs, int ntubes,
+                                                          const double *rho, const double *ux,
+                                                          const double *uy, const double *T, TS *f,
+                                                          unsigned *flag)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.P;
+         c += (long long)gridDim.x * blockDim.x) {
+        const TubeInfo &t = tubes[tube_of(offs, ntubes, c)];
+        const ClassConsts &C = a.cls[t.cls];
+        const double r = rho[c], u = ux[c], v = uy[c], tt = T[c];
+        const double jx = r * u, jy = r * v;
+        const double jyuy = jy * v;
+        const double ru2 = fma(jx, u, jyuy);
+        const double p = r * tt;
+        const double E = fma(C.m.K, p, ru2);
+        double fe[kNV];
+        equilibrium(C.unit, C.m, r, E, jx, jy, u, v, ru2, jyuy, p, tt, fe);
+        if (!(positive_finite(r) && positive_finite(tt) && isfinite(u) && isfinite(v)))
+            atomicOr(flag, kFlagNonPhys);
+#pragma unroll
+        for (int i = 0; i < kNV; ++i) {
+            if constexpr (kSingle<TS>)
+                f[i * a.P + c] = (float)(fe[i] - t.Fg[i >> 2]);
+            else
+                f[i * a.P + c] = fe[i];
+        }
+    }
+}
+
+template <typename TS>
+__global__ void __launch_bounds__(128) batch_macros_kernel(const BatchArgs a, const TubeInfo *tubes,
+                                                            const long long *offs, int ntubes, const TS *f,
+                                                            double *rho, double *ux, double *uy, double *T)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.P;
+         c += (long long)gridDim.x * blockDim.x) {
+        const TubeInfo &t = tubes[tube_of(offs, ntubes, c)];
+        const ModelConsts &m = a.cls[t.cls].m;
+        double fc[kNV];
+#pragma unroll
+        for (int i = 0; i < kNV; ++i)
+            fc[i] = kSingle<TS> ? t.Fg[i >> 2] + (double)f[i * a.P + c] : (double)f[i * a.P + c];
+        const Cons q = conserved(fc, m);
+        const double u = q.jx / q.rho, v = q.jy / q.rho;
+        const double ru2 = fma(q.jx, u, q.jy * v);
+        if (rho) rho[c] = q.rho;
+        if (ux) ux[c] = u;
+        if (uy) uy[c] = v;
+        if (T) T[c] = (q.E - ru2) / (m.K * q.rho);
+    }
+}
+
+template <typename TS>
+void *batch_func(int threads)
+{
+    switch (threads) {
+    case 64: return (void *)batch_kernel<TS, 64>;
+    case 256: return (void *)batch_kernel<TS, 256>;
+    default: return (void *)batch_kernel<TS, 128>;
+    }
+}
+
+}  // namespace
+
+struct cdbm_batch {
+    int ntubes, precision;
+    long long P;
+    double tau, dt;
+    cudaStream_t stream;
+    cdbm_allocator alloc;
+    bool user_alloc;
+    int sm_count;
+    std::vector<int> nx;
+    std::vector<long long> offs;       // ntubes + 1
+    std::vector<TubeInfo> info;
+    std::vector<double> Ivals;         // distinct I per class
+    BatchArgs args;
+    void *f, *f1;
+    TubeInfo *d_tubes;
+    long long *d_offs;
+    int *d_work, *d_work_off;          // partition: tube ids per block (CSR)
+    unsigned *flag;
+    unsigned *flag_host;
+    int threads, blocks;               // current tile: threads per block, number of blocks
+    bool state_set;
+    double t;
+    cudaGraphExec_t graph;
+    int graph_steps;
+    cdbm_status err;
+    char msg[256];
+};
+
+namespace {
+
+cdbm_status bset_err(cdbm_batch *b, cdbm_status s, const char *fmt, ...)
+{
+    if (b->err != CDBM_OK) return b->err;
+    b->err = s;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(b->msg, sizeof(b->msg), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+cdbm_status bcreate_err(cdbm_status s, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(thread_error_buffer(), kThreadErrorBytes, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+cdbm_status bcuda(cdbm_batch *b, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return CDBM_OK;
+    cudaGetLastError();
+    return bset_err(b, CDBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void *balloc(cdbm_batch *b, size_t bytes)
+{
+    if (b->user_alloc) return b->alloc.alloc(bytes, (void *)b->stream, b->alloc.user);
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void bfree(cdbm_batch *b, void *p, size_t bytes)
+{
+    if (!p) return;
+    if (b->user_alloc)
+        b->alloc.free(p, bytes, (void *)b->stream, b->alloc.user);
+    else
+        cudaFreeAsync(p, b->stream);
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+void drop_batch_graph(cdbm_batch *b)
+{
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+}
+
+// Longest-first partition of the tubes over nblocks blocks; a tube's cost is the
+// number of cell slots its stages occupy, ceil(nx / threads) * threads.
+void partition(const cdbm_batch *b, int threads, int nblocks, std::vector<int> &work, std::vector<int> &off)
+{
+    std::vector<int> order(b->ntubes);
+    std::iota(order.begin(), order.end(), 0);
+    auto cost = [&](int t) { return (long long)((b->nx[t] + threads - 1) / threads) * threads; };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    std::vector<long long> load(nblocks, 0);
+    std::vector<std::vector<int>> lists(nblocks);
+    for (int t : order) {
+        int best = 0;
+        for (int k = 1; k < nblocks; ++k)
+            if (load[k] < load[best]) best = k;
+        load[best] += cost(t);
+        lists[best].push_back(t);
+    }
+    work.clear();
+    off.assign(1, 0);
+    for (int k = 0; k < nblocks; ++k) {
+        for (int t : lists[k]) work.push_back(t);
+        off.push_back((int)work.size());
+    }
+}
+
+cdbm_status set_tile(cdbm_batch *b, int threads, int blocks_per_sm)
+{
+    const int nblocks = std::max(1, std::min(b->ntubes, blocks_per_sm * b->sm_count));
+    std::vector<int> work, off;
+    partition(b, threads, nblocks, work, off);
+    bfree(b, b->d_work, 0);
+    bfree(b, b->d_work_off, 0);
+    b->d_work = (int *)balloc(b, sizeof(int) * work.size());
+    b->d_work_off = (int *)balloc(b, sizeof(int) * off.size());
+    if (!b->d_work || !b->d_work_off) return bset_err(b, CDBM_ENOMEM, "work list allocation failed");
+    if (bcuda(b, cudaMemcpyAsync(b->d_work, work.data(), sizeof(int) * work.size(), cudaMemcpyHostToDevice,
+                                 b->stream), "work upload") ||
+        bcuda(b, cudaMemcpyAsync(b->d_work_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice,
+                                 b->stream), "work upload") ||
+        bcuda(b, cudaStreamSynchronize(b->stream), "work upload sync"))
+        return b->err;
+    b->threads = threads;
+    b->blocks = nblocks;
+    drop_batch_graph(b);
+    return CDBM_OK;
+}
+
+cdbm_status launch_run(cdbm_batch *b, int nsteps)
+{
+    void *f = b->f, *f1 = b->f1;
+    const TubeInfo *tubes = b->d_tubes;
+    const int *work = b->d_work, *off = b->d_work_off;
+    void *args[] = {&f, &f1, (void *)&tubes, (void *)&work, (void *)&off, &nsteps, (void *)&b->args, &b->flag};
+    void *fn = b->precision == CDBM_FP32_BULK ? batch_func<float>(b->threads) : batch_func<double>(b->threads);
+    return bcuda(b, cudaLaunchKernel(fn, dim3(b->blocks), dim3(b->threads), args, 0, b->stream), "batch launch");
+}
+
+// One persistent launch of nsteps steps, replayed from an explicitly built graph.
+cdbm_status run_graph(cdbm_batch *b, int nsteps)
+{
+    if (!b->graph || b->graph_steps != nsteps) {
+        drop_batch_graph(b);
+        void *f = b->f, *f1 = b->f1;
+        const TubeInfo *tubes = b->d_tubes;
+        const int *work = b->d_work, *off = b->d_work_off;
+        void *args[] = {&f, &f1, (void *)&tubes, (void *)&work, (void *)&off, &nsteps, (void *)&b->args, &b->flag};
+        cudaKernelNodeParams p;
+        memset(&p, 0, sizeof(p));
+        p.func = b->precision == CDBM_FP32_BULK ? batch_func<float>(b->threads) : batch_func<double>(b->threads);
+        p.gridDim = dim3(b->blocks);
+        p.blockDim = dim3(b->threads);
+        p.kernelParams = args;
+        cudaGraph_t g;
+        cudaGraphNode_t node;
+        if (bcuda(b, cudaGraphCreate(&g, 0), "graph create")) return b->err;
+        cudaError_t e = cudaGraphAddKernelNode(&node, g, nullptr, 0, &p);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            b->graph = nullptr;
+            return bcuda(b, e, "graph build");
+        }
+        b->graph_steps = nsteps;
+    }
+    return bcuda(b, cudaGraphLaunch(b->graph, b->stream), "graph launch");
+}
+
+unsigned cells_grid(long long n) { return (unsigned)std::max<long long>(1, std::min<long long>((n + 127) / 128, 1 << 20)); }
+
+}  // namespace
+
+extern "C" {
+
+cdbm_status cdbm_batch_create(int ntubes, const int *nx, const double *dx, const double *I,
+                              const cdbm_vset *vset, double tau, double dt, int precision, void *cuda_stream,
+                              const cdbm_allocator *allocator, cdbm_batch **out)
+{
+    if (!out) return bcreate_err(CDBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (ntubes < 1 || !nx || !dx || !I || !vset) return bcreate_err(CDBM_EINVAL, "batch: bad arguments");
+    if (!(std::isfinite(dt) && dt > 0 && std::isfinite(tau) && tau > 0))
+        return bcreate_err(CDBM_EINVAL, "dt and tau must be finite and > 0");
+    if (dt / tau > 2.0) return bcreate_err(CDBM_EINVAL, "dt/tau = %g exceeds 2", dt / tau);
+    if (precision != CDBM_FP64 && precision != CDBM_FP32_BULK)
+        return bcreate_err(CDBM_EINVAL, "unsupported precision %d", precision);
+    double vmax = 0.0;
+    for (int g = 0; g < 4; ++g) {
+        if (!std::isfinite(vset->v[g]) || !std::isfinite(vset->eta[g]) || vset->v[g] <= 0 || vset->eta[g] < 0)
+            return bcreate_err(CDBM_EINVAL, "velocity set: v must be > 0 and eta >= 0");
+        vmax = std::max(vmax, vset->v[g]);
+    }
+    cdbm_batch *b = new (std::nothrow) cdbm_batch();
+    if (!b) return bcreate_err(CDBM_ENOMEM, "host allocation failed");
+    b->ntubes = ntubes;
+    b->precision = precision;
+    b->tau = tau;
+    b->dt = dt;
+    b->stream = (cudaStream_t)cuda_stream;
+    b->user_alloc = allocator && allocator->alloc && allocator->free;
+    if (b->user_alloc) b->alloc = *allocator;
+    b->err = CDBM_OK;
+    strcpy(b->msg, "no error");
+    b->nx.assign(nx, nx + ntubes);
+    b->offs.assign(ntubes + 1, 0);
+    b->info.resize(ntubes);
+    const double h = dt / tau;
+    const double alpha[2] = {0.0, 0.5}, beta[2] = {1.0, 0.5}, gamma[2] = {1.0, 0.5};
+    for (int s = 0; s < 2; ++s) {
+        b->args.a_self[s] = beta[s] - gamma[s] * h;
+        b->args.a_base[s] = alpha[s];
+        b->args.a_self_f[s] = (float)b->args.a_self[s];
+        b->args.a_base_f[s] = (float)b->args.a_base[s];
+    }
+    for (int t = 0; t < ntubes; ++t) {
+        if (nx[t] < 1 || !(std::isfinite(dx[t]) && dx[t] > 0) || !(std::isfinite(I[t]) && I[t] >= 0)) {
+            delete b;
+            return bcreate_err(CDBM_EINVAL, "tube %d: nx, dx or I invalid", t);
+        }
+        if (nx[t] > 1 && vmax * dt / dx[t] > 1.0) {
+            delete b;
+            return bcreate_err(CDBM_EINVAL, "tube %d: CFL number %g exceeds 1", t, vmax * dt / dx[t]);
+        }
+        int cls = -1;
+        for (size_t k = 0; k < b->Ivals.size(); ++k)
+            if (b->Ivals[k] == I[t]) cls = (int)k;
+        if (cls < 0) {
+            if ((int)b->Ivals.size() == kMaxClasses) {
+                delete b;
+                return bcreate_err(CDBM_EINVAL, "batch: more than %d distinct values of I", kMaxClasses);
+            }
+            cls = (int)b->Ivals.size();
+            b->Ivals.push_back(I[t]);
+            ClassConsts &C = b->args.cls[cls];
+            double cond = 0.0;
+            const char *which = "";
+            if (build_blocks(*vset, I[t], C.m, C.unit, &cond, &which) != CDBM_OK) {
+                delete b;
+                return bcreate_err(CDBM_ESINGULAR, "moment matrix block '%s' singular (cond %g)", which, cond);
+            }
+            for (int s = 0; s < 2; ++s) C.eq[s] = scaled(C.unit, gamma[s] * h);
+        }
+        TubeInfo &ti = b->info[t];
+        memset(&ti, 0, sizeof(ti));
+        ti.offset = b->offs[t];
+        ti.nx = nx[t];
+        ti.cls = cls;
+        for (int s = 0; s < 2; ++s)
+            for (int g = 0; g < 4; ++g) {
+                ti.lx[s][g] = gamma[s] * dt * vset->v[g] / dx[t];
+                ti.lx_f[s][g] = (float)ti.lx[s][g];
+            }
+        b->offs[t + 1] = b->offs[t] + nx[t];
+    }
+    b->P = b->offs[ntubes];
+    b->args.P = b->P;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return bcreate_err(CDBM_ECUDA, "no CUDA device");
+    }
+    const size_t fb = storage_bytes(precision) * kNV * (size_t)b->P;
+    b->f = balloc(b, fb);
+    b->f1 = balloc(b, fb);
+    b->d_tubes = (TubeInfo *)balloc(b, sizeof(TubeInfo) * ntubes);
+    b->d_offs = (long long *)balloc(b, sizeof(long long) * (ntubes + 1));
+    b->flag = (unsigned *)balloc(b, 256);
+    if (!b->f || !b->f1 || !b->d_tubes || !b->d_offs || !b->flag ||
+        cudaMallocHost(&b->flag_host, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        cdbm_batch_destroy(b);
+        return bcreate_err(CDBM_ENOMEM, "batch device allocation failed");
+    }
+    if (cudaMemsetAsync(b->flag, 0, sizeof(unsigned), b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(b->d_offs, b->offs.data(), sizeof(long long) * (ntubes + 1), cudaMemcpyHostToDevice,
+                        b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(b->d_tubes, b->info.data(), sizeof(TubeInfo) * ntubes, cudaMemcpyHostToDevice,
+                        b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        cdbm_batch_destroy(b);
+        return bcreate_err(CDBM_ECUDA, "batch upload failed");
+    }
+    if (set_tile(b, 128, 3) != CDBM_OK) {
+        cdbm_status s = b->err;
+        cdbm_batch_destroy(b);
+        return bcreate_err(s, "batch work partition failed");
+    }
+    *out = b;
+    return CDBM_OK;
+}
+
+cdbm_status cdbm_batch_init(cdbm_batch *b, const double *rho, const double *ux, const double *uy, const double *T)
+{
+    if (!b) return CDBM_EINVAL;
+    if (b->err) return b->err;
+    if (!rho || !ux || !uy || !T) return bset_err(b, CDBM_EINVAL, "cdbm_batch_init: NULL field");
+    const size_t n = (size_t)b->P;
+    const double *src[4] = {rho, ux, uy, T};
+    std::vector<double> host[4];
+    const double *dev[4];
+    // the second buffer (16 planes of the storage type) stages host fields: 4 double planes fit
+    double *stage = (double *)b->f1;
+    for (int k = 0; k < 4; ++k) {
+        host[k].resize(n);
+        if (bcuda(b, cudaMemcpy(host[k].data(), src[k], sizeof(double) * n, cudaMemcpyDefault), "batch fields read"))
+            return b->err;
+        if (is_device_ptr(src[k])) {
+            dev[k] = src[k];
+        } else {
+            if (bcuda(b, cudaMemcpyAsync(stage + k * n, src[k], sizeof(double) * n, cudaMemcpyHostToDevice,
+                                         b->stream), "batch fields upload"))
+                return b->err;
+            dev[k] = stage + k * n;
+        }
+    }
+    // per-tube reference state (FP32-bulk): means of rho and T over the tube
+    for (int t = 0; t < b->ntubes; ++t) {
+        TubeInfo &ti = b->info[t];
+        const ClassConsts &C = b->args.cls[ti.cls];
+        double sr = 0.0, sT = 0.0;
+        for (long long c = b->offs[t]; c < b->offs[t + 1]; ++c) {
+            sr += host[0][c];
+            sT += host[3][c];
+        }
+        const double r0 = sr / ti.nx, T0 = sT / ti.nx, K = C.m.K, P0 = r0 * T0;
+        ti.rhoF = ti.EF = 0.0;
+        for (int g = 0; g < 4; ++g) {
+            const double *S = C.unit.S + 4 * g;
+            ti.Fg[g] = b->precision == CDBM_FP32_BULK
+                           ? S[0] * r0 + S[1] * K * P0 + S[3] * 2.0 * (K + 2.0) * P0 * T0
+                           : 0.0;
+            ti.rhoF += 4.0 * ti.Fg[g];
+            ti.EF += 4.0 * ti.Fg[g] * C.m.w[g];
+        }
+        const double h = b->dt / b->tau, gamma[2] = {1.0, 0.5};
+        for (int s = 0; s < 2; ++s)
+            for (int g = 0; g < 4; ++g) ti.sF[s][g] = gamma[s] * h * ti.Fg[g];
+    }
+    const unsigned nb = cells_grid(b->P);
+    if (bcuda(b, cudaMemcpyAsync(b->d_tubes, b->info.data(), sizeof(TubeInfo) * b->ntubes, cudaMemcpyHostToDevice,
+                                 b->stream), "tube upload"))
+        return b->err;
+    if (b->precision == CDBM_FP32_BULK)
+        batch_init_kernel<float><<<nb, 128, 0, b->stream>>>(b->args, b->d_tubes, b->d_offs, b->ntubes, dev[0], dev[1],
+                                                            dev[2], dev[3], (float *)b->f, b->flag);
+    else
+        batch_init_kernel<double><<<nb, 128, 0, b->stream>>>(b->args, b->d_tubes, b->d_offs, b->ntubes, dev[0],
+                                                             dev[1], dev[2], dev[3], (double *)b->f, b->flag);
+    if (bcuda(b, cudaGetLastError(), "batch init launch") || bcuda(b, cudaStreamSynchronize(b->stream), "batch init sync"))
+        return b->err;
+    b->t = 0.0;
+    b->state_set = true;
+    return CDBM_OK;
+}
+
+cdbm_status cdbm_batch_step(cdbm_batch *b, int nsteps)
+{
+    if (!b) return CDBM_EINVAL;
+    if (b->err) return b->err;
+    if (nsteps < 0) return bset_err(b, CDBM_EINVAL, "cdbm_batch_step: nsteps < 0");
+    if (!b->state_set) return bset_err(b, CDBM_EINVAL, "cdbm_batch_step: state not initialised");
+    if (nsteps == 0) return CDBM_OK;
+    if (run_graph(b, nsteps)) return b->err;
+    b->t += nsteps * b->dt;
+    return CDBM_OK;
+}
+
+cdbm_status cdbm_batch_autotune(cdbm_batch *b, int trial_steps, int *threads_out, int *blocks_per_sm_out)
+{
+    if (!b) return CDBM_EINVAL;
+    if (b->err) return b->err;
+    if (!b->state_set) return bset_err(b, CDBM_EINVAL, "cdbm_batch_autotune: state not initialised");
+    if (trial_steps < 1) trial_steps = 1;
+    // The trials advance the state; it is saved and restored around them.
+    const size_t fb = storage_bytes(b->precision) * kNV * (size_t)b->P;
+    void *save = balloc(b, fb);
+    if (!save) return bset_err(b, CDBM_ENOMEM, "autotune backup allocation failed");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int cand_threads[3] = {64, 128, 256};
+    const int cand_bpsm[4] = {1, 2, 3, 4};
+    float best = 1e30f;
+    int bt = b->threads, bb = 3;
+    cdbm_status st = CDBM_OK;
+    if (bcuda(b, cudaMemcpyAsync(save, b->f, fb, cudaMemcpyDeviceToDevice, b->stream), "autotune backup"))
+        st = b->err;
+    for (int i = 0; i < 3 && st == CDBM_OK; ++i)
+        for (int j = 0; j < 4 && st == CDBM_OK; ++j) {
+            if (cand_threads[i] * cand_bpsm[j] > 1024) continue;
+            if ((st = set_tile(b, cand_threads[i], cand_bpsm[j])) != CDBM_OK) break;
+            if ((st = launch_run(b, 1)) != CDBM_OK) break;        // warm-up
+            cudaEventRecord(e0, b->stream);
+            if ((st = launch_run(b, trial_steps)) != CDBM_OK) break;
+            cudaEventRecord(e1, b->stream);
+            if ((st = bcuda(b, cudaEventSynchronize(e1), "autotune sync")) != CDBM_OK) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bt = cand_threads[i];
+                bb = cand_bpsm[j];
+            }
+            if ((st = bcuda(b, cudaMemcpyAsync(b->f, save, fb, cudaMemcpyDeviceToDevice, b->stream),
+                            "autotune restore")) != CDBM_OK)
+                break;
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    bfree(b, save, fb);
+    if (st != CDBM_OK) return st;
+    if (set_tile(b, bt, bb)) return b->err;
+    if (bcuda(b, cudaMemsetAsync(b->flag, 0, sizeof(unsigned), b->stream), "flag reset")) return b->err;
+    if (threads_out) *threads_out = bt;
+    if (blocks_per_sm_out) *blocks_per_sm_out = bb;
+    return CDBM_OK;
+}
+
+cdbm_status cdbm_batch_set_tile(cdbm_batch *b, int threads, int blocks_per_sm)
+{
+    if (!b) return CDBM_EINVAL;
+    if (b->err) return b->err;
+    if ((threads != 64 && threads != 128 && threads != 256) || blocks_per_sm < 1 || blocks_per_sm > 16)
+        return bset_err(b, CDBM_EINVAL, "tile: threads must be 64, 128 or 256 and blocks_per_sm in 1..16");
+    return set_tile(b, threads, blocks_per_sm);
+}
+
+cdbm_status cdbm_batch_macros(cdbm_batch *b, double *rho, double *ux, double *uy, double *T)
+{
+    if (!b) return CDBM_EINVAL;
+    if (b->err) return b->err;
+    if (!b->state_set) return bset_err(b, CDBM_EINVAL, "cdbm_batch_macros: state not initialised");
+    const size_t n = (size_t)b->P;
+    double *dst[4] = {rho, ux, uy, T};
+    double *dev[4];
+    bool host[4];
+    double *stage = (double *)b->f1;
+    for (int k = 0; k < 4; ++k) {
+        host[k] = dst[k] && !is_device_ptr(dst[k]);
+        dev[k] = host[k] ? stage + k * n : dst[k];
+    }
+    const unsigned nb = cells_grid(b->P);
+    if (b->precision == CDBM_FP32_BULK)
+        batch_macros_kernel<float><<<nb, 128, 0, b->stream>>>(b->args, b->d_tubes, b->d_offs, b->ntubes,
+                                                              (const float *)b->f, dev[0], dev[1], dev[2], dev[3]);
+    else
+        batch_macros_kernel<double><<<nb, 128, 0, b->stream>>>(b->args, b->d_tubes, b->d_offs, b->ntubes,
+                                                               (const double *)b->f, dev[0], dev[1], dev[2], dev[3]);
+    if (bcuda(b, cudaGetLastError(), "batch macros launch")) return b->err;
+    for (int k = 0; k < 4; ++k)
+        if (host[k] && bcuda(b, cudaMemcpyAsync(dst[k], dev[k], sizeof(double) * n, cudaMemcpyDeviceToHost,
+                                                b->stream), "batch macros download"))
+            return b->err;
+    return bcuda(b, cudaStreamSynchronize(b->stream), "batch macros sync");
+}
+
+cdbm_status cdbm_batch_sync(cdbm_batch *b)
+{
+    if (!b) return CDBM_EINVAL;
+    if (b->err) return b->err;
+    if (bcuda(b, cudaMemcpyAsync(b->flag_host, b->flag, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream),
+              "flag download") ||
+        bcuda(b, cudaStreamSynchronize(b->stream), "cdbm_batch_sync"))
+        return b->err;
+    if (*b->flag_host & kFlagNonPhys)
+        return bset_err(b, CDBM_ENONPHYS, "non-physical state (rho <= 0, T <= 0 or non-finite) at t = %g", b->t);
+    return CDBM_OK;
+}
+
+cdbm_status cdbm_batch_info(const cdbm_batch *b, long long *total_cells, int *threads, int *blocks)
+{
+    if (!b) return CDBM_EINVAL;
+    if (total_cells) *total_cells = b->P;
+    if (threads) *threads = b->threads;
+    if (blocks) *blocks = b->blocks;
+    return b->err;
+}
+
+const char *cdbm_batch_last_error(const cdbm_batch *b) { return b ? b->msg : thread_error_buffer(); }
+
+void cdbm_batch_destroy(cdbm_batch *b)
+{
+    if (!b) return;
+    drop_batch_graph(b);
+    const size_t fb = storage_bytes(b->precision) * kNV * (size_t)b->P;
+    bfree(b, b->f, fb);
+    bfree(b, b->f1, fb);
+    bfree(b, b->d_tubes, 0);
+    bfree(b, b->d_offs, 0);
+    bfree(b, b->flag, 256);
+    bfree(b, b->d_work, 0);
+    bfree(b, b->d_work_off, 0);
+    cudaStreamSynchronize(b->stream);
+    if (b->flag_host) cudaFreeHost(b->flag_host);
+    cudaGetLastError();
+    delete b;
+}
+
+}  // extern "C"

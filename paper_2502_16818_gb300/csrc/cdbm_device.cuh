@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "cdbm_internal.h"
 
@@ -180,6 +181,41 @@ __device__ __forceinline__ void equilibrium(const EqBlocks &B, const ModelConsts
     rebuild_diag(out + 4, s0[1], qb, sx[1], sy[1]);
     rebuild_axis(out + 8, s0[2], dqc, sx[2], sy[2]);
     rebuild_diag(out + 12, s0[3], qd, sx[3], sy[3]);
+}
+
+template <typename TS>
+constexpr bool kSingle = std::is_same<TS, float>::value;
+
+__device__ __forceinline__ double fma_t(double x, double y, double z) { return fma(x, y, z); }
+__device__ __forceinline__ float fma_t(float x, float y, float z) { return fmaf(x, y, z); }
+
+// Per-cell macroscopic quantities of a stage: conserved moments (in double), then
+// u, P = rho T and T through the refined reciprocal of rho.  With kShift, f holds
+// g = f - F and the reference moments rhoF, EF are added.
+struct Prim {
+    Cons q;
+    double ux, uy, jyuy, ru2, p, T;
+};
+
+template <bool kShift>
+__device__ __forceinline__ Prim primitives(const double f[kNV], const ModelConsts &m, double rhoF,
+                                           double EF, unsigned *flag)
+{
+    Prim s;
+    s.q = conserved(f, m);
+    if (kShift) {
+        s.q.rho += rhoF;
+        s.q.E += EF;
+    }
+    const double r = rcp64(s.q.rho);
+    s.ux = s.q.jx * r;
+    s.uy = s.q.jy * r;
+    s.jyuy = s.q.jy * s.uy;
+    s.ru2 = fma(s.q.jx, s.ux, s.jyuy);
+    s.p = (s.q.E - s.ru2) * m.invK;
+    s.T = s.p * r;
+    if (!(positive_finite(s.q.rho) && positive_finite(s.p))) atomicOr(flag, kFlagNonPhys);
+    return s;
 }
 
 // Neighbour index along an axis of n cells: periodic wrap or zero-gradient clamp.

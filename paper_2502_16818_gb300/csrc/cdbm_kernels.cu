@@ -8,8 +8,6 @@
 // one cell; a block covers a run of cells along x of one row, so centre loads
 // and stores of a warp are coalesced rows and the stencil neighbours
 // (x +- 1, 2 and the rows y +- 1, 2) are served from L1/L2.
-#include <type_traits>
-
 #include "cdbm_device.cuh"
 
 namespace cdbm {
@@ -20,9 +18,6 @@ constexpr int kStageThreads = 128;
 #ifndef CDBM_STAGE_MIN_BLOCKS
 #define CDBM_STAGE_MIN_BLOCKS 3   // resident stage blocks per SM the register budget must allow
 #endif
-
-template <typename TS>
-constexpr bool kSingle = std::is_same<TS, float>::value;
 
 // Stage coefficients in the storage precision.
 template <typename TS>
@@ -45,9 +40,6 @@ __device__ __forceinline__ TS ly_of(const StageArgs &a, int g)
 {
     if constexpr (kSingle<TS>) return a.ly_f[g]; else return a.ly[g];
 }
-
-__device__ __forceinline__ double fma_t(double x, double y, double z) { return fma(x, y, z); }
-__device__ __forceinline__ float fma_t(float x, float y, float z) { return fmaf(x, y, z); }
 
 // Stored value of velocity i -> f_i in double (adds the reference F to an FP32 deviation).
 __device__ __forceinline__ double widen(const FieldArgs &, double v, int) { return v; }
@@ -83,35 +75,6 @@ __global__ void __launch_bounds__(128) init_kernel(const FieldArgs a, const doub
                 f[i * P + c] = fe[i];
         }
     }
-}
-
-// Per-cell macroscopic quantities of the stage: conserved moments (in double),
-// then u, P = rho T and T through the refined reciprocal of rho.
-struct Prim {
-    Cons q;
-    double ux, uy, jyuy, ru2, p, T;
-};
-
-// With kShift, f holds g = f - F and the reference moments rhoF, EF are added.
-template <bool kShift>
-__device__ __forceinline__ Prim primitives(const double f[kNV], const ModelConsts &m, double rhoF,
-                                           double EF, unsigned *flag)
-{
-    Prim s;
-    s.q = conserved(f, m);
-    if (kShift) {
-        s.q.rho += rhoF;
-        s.q.E += EF;
-    }
-    const double r = rcp64(s.q.rho);
-    s.ux = s.q.jx * r;
-    s.uy = s.q.jy * r;
-    s.jyuy = s.q.jy * s.uy;
-    s.ru2 = fma(s.q.jx, s.ux, s.jyuy);
-    s.p = (s.q.E - s.ru2) * m.invK;
-    s.T = s.p * r;
-    if (!(positive_finite(s.q.rho) && positive_finite(s.p))) atomicOr(flag, kFlagNonPhys);
-    return s;
 }
 
 // ------------------------------------------------------------ RK stage (K1/K2)

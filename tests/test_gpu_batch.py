@@ -1,0 +1,132 @@
+"""Batched ensembles of shock tubes (cdbm_batch_*) against the CPU oracle.
+
+Each tube of a batch is an independent Ny = 1 run; the oracle runs every checked
+tube on its own.  Acceptance: FP64 batch <= 1e-10 relative max-norm on rho, u, T
+(as the single-grid path); FP32-bulk batch <= 1e-5 relative L2 density error.
+The result of a batch does not depend on its tile (threads per block, partition):
+each cell's arithmetic is the same, so states agree bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_16818_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_16818_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+
+
+def tubes_small(n=12, seed=3, steps=200):
+    specs = W.ensemble_draw(n, seed=seed, nx_lo=20, nx_hi=300)
+    return [W.ensemble_tube(s, steps=steps) for s in specs]
+
+
+def oracle_tube(w, steps):
+    m = oracle.Model(nx=w.nx, ny=1, dx=w.dx, dy=w.dy, dt=w.dt, tau=w.tau, I=w.I, vg=w.vg, eg=w.eg,
+                     bc_x=w.bc_x, bc_y=w.bc_y)
+    return oracle.macros(m, oracle.step(m, oracle.init(m, w.rho, w.ux, w.uy, w.T), steps))
+
+
+def run_batch(tubes, steps, precision=0, tile=None, autotune=False):
+    from paper_2502_16818_gb300 import BatchSolver
+    b = BatchSolver(tubes, precision=precision)
+    b.init(tubes)
+    if tile:
+        b.set_tile(*tile)
+    if autotune:
+        b.autotune(3)
+    b.step(steps)
+    b.sync()
+    out = b.macros()
+    b.close()
+    return b, out
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def test_batch_fp64_matches_oracle_per_tube():
+    tubes = tubes_small()
+    b, out = run_batch(tubes, 200)
+    for t, w in enumerate(tubes):
+        got = b.tube(out, t)
+        ref = oracle_tube(w, 200)
+        us = max(np.abs(ref[1]).max(), 1e-300)
+        assert rel(got[0], ref[0][0]) <= 1e-10, t
+        assert np.abs(got[1] - ref[1][0]).max() / us <= 1e-10, t
+        assert rel(got[3], ref[3][0]) <= 1e-10, t
+
+
+def test_batch_fp32_bulk_matches_oracle_per_tube():
+    from paper_2502_16818_gb300 import CDBM_FP32_BULK
+    tubes = tubes_small(seed=4)
+    b, out = run_batch(tubes, 200, precision=CDBM_FP32_BULK)
+    for t, w in enumerate(tubes):
+        got = b.tube(out, t)
+        ref = oracle_tube(w, 200)
+        l2 = np.linalg.norm(got[0] - ref[0][0]) / np.linalg.norm(ref[0][0])
+        assert l2 <= 1e-5, (t, l2)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_result_independent_of_tile(precision):
+    tubes = tubes_small(n=40, seed=5, steps=30)
+    outs = [run_batch(tubes, 30, precision, tile=tile)[1] for tile in ((64, 1), (128, 3), (256, 4))]
+    outs.append(run_batch(tubes, 30, precision, autotune=True)[1])
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(a, b)
+
+
+def test_batch_matches_single_grid_path():
+    from paper_2502_16818_gb300 import Solver
+    tubes = tubes_small(n=6, seed=6, steps=50)
+    b, out = run_batch(tubes, 50)
+    for t, w in enumerate(tubes):
+        s = Solver.from_workload(w)
+        s.init(w.rho, w.ux, w.uy, w.T)
+        s.step(50)
+        single = [x.cpu().numpy()[0] for x in s.macros()]
+        s.close()
+        for a, c in zip(b.tube(out, t), single):
+            assert np.array_equal(a, c)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_ensemble_sampled_tubes(precision):
+    """The configured ensemble: 1024 tubes, Nx ~ U{200..4000} (seed 0), 1000 steps,
+    autotuned tile; four tubes (shortest, longest, two others) checked against the
+    oracle."""
+    specs = W.ensemble_draw(1024, seed=0)
+    tubes = [W.ensemble_tube(s, steps=1000) for s in specs]
+    b, out = run_batch(tubes, 1000, precision, autotune=True)
+    nx = np.array([w.nx for w in tubes])
+    for t in sorted({int(nx.argmin()), int(nx.argmax()), 17, 600}):
+        got = b.tube(out, t)
+        ref = oracle_tube(tubes[t], 1000)
+        if precision == 0:
+            assert rel(got[0], ref[0][0]) <= 1e-10 and rel(got[3], ref[3][0]) <= 1e-10, t
+        else:
+            l2 = np.linalg.norm(got[0] - ref[0][0]) / np.linalg.norm(ref[0][0])
+            assert l2 <= 1e-5, (t, l2)
+
+
+def test_batch_rejects_bad_input():
+    from paper_2502_16818_gb300 import CdbmError, BatchSolver
+    w = tubes_small(n=2)
+    bad = W.ensemble_tube({"nx": 100000, "rho": (1, 1), "T": (1, 1), "I": 0.0})   # CFL 5
+    with pytest.raises(CdbmError, match="CFL"):
+        BatchSolver([w[0], bad])
+    many_I = [W.ensemble_tube({"nx": 30, "rho": (1, 0.5), "T": (1, 1), "I": float(k)}) for k in range(5)]
+    with pytest.raises(CdbmError, match="distinct values of I"):
+        BatchSolver(many_I)
