@@ -33,13 +33,13 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-updates/s and HBM GB/s vs FP64 plain on same GB300 at stated L2 error"
 UNIT = "cell-updates/s"
 
-# FP64 work of the fused stage kernels per cell.  Instructions: ncu
-# sm__inst_executed_pipe_fp64 per warp of 32 cells (stage 1: 293, stage 2: 309).
-# Flops, counted from the kernel source with an FMA as two flops: stage 1: 424,
-# stage 2: 456.  Bytes per cell-step: stage 1 reads f^n and writes f1 (128 + 128 B);
+# FP64 work of the fused (row-marching) stage kernels per cell.  Instructions: ncu
+# sm__inst_executed_pipe_fp64 per warp of 32 cells (stage 1: 272, stage 2: 288).
+# Flops, counted from the kernel source with an FMA as two flops: stage 1: 400,
+# stage 2: 432.  Bytes per cell-step: stage 1 reads f^n and writes f1 (128 + 128 B);
 # stage 2 reads f1 and f^n and writes f^n+1 (384 B).
-FP64_INSTR_PER_CELL_STEP = 602
-FP64_FLOPS_PER_CELL_STEP = 880
+FP64_INSTR_PER_CELL_STEP = 560
+FP64_FLOPS_PER_CELL_STEP = 832
 BYTES_PER_CELL_STEP = 640
 FP64_LANES_PER_CLK_PER_SM = 2       # 1.25 TFLOP/s nominal FP64 / (2 flops x 152 SMs x 2.07 GHz)
 
@@ -47,11 +47,11 @@ FP64_LANES_PER_CLK_PER_SM = 2       # 1.25 TFLOP/s nominal FP64 / (2 flops x 152
 # the stage kernels; valid only while the kernel sources hash to TRAFFIC_SHA.
 # Captured at 1024^2 (134 MB per plane set, above L2) and scaled by 16 cells-fold; see
 # profiles/stage_kernel_tgv.md.
-TRAFFIC_SHA = "11a587991b9001d0"
-TRAFFIC_BYTES_PER_LAUNCH = 4.784e9
+TRAFFIC_SHA = "4a03d10916753b49"
+TRAFFIC_BYTES_PER_LAUNCH = 5.097e9
 
 
-STAGE_SOURCES = ("cdbm_device.cuh", "cdbm_kernels.cu")
+STAGE_SOURCES = ("cdbm_device.cuh", "cdbm_kernels.cu", "cdbm_internal.h")
 
 
 def kernel_sha():
@@ -73,6 +73,8 @@ def parse():
     p.add_argument("--n", type=int, default=4096, help="grid size (n x n)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-variants", action="store_true", help="skip the FP32-bulk and ensemble runs")
+    p.add_argument("--ens-steps", type=int, default=200, help="timed steps of the tube ensemble")
     return p.parse_args()
 
 
@@ -182,24 +184,40 @@ def run_reference(a, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def tgv_amplitude(w, ux):
+    """Projection of u_x onto sin(kx) cos(ky) (the Taylor-Green mode)."""
+    import torch
+    k = w.extra["k"]
+    x = (torch.arange(w.nx, dtype=torch.float64, device=ux.device) + 0.5) * w.dx
+    return float((ux * torch.cos(k * x)[:, None] * torch.sin(k * x)[None, :]).sum())
+
+
+def time_tgv(w, precision, steps, warmup, torch, Solver):
+    """A solver for the vortex on its own stream, initialised and warmed up; returns
+    (solver, stream, Taylor-Green amplitude of u_x after the warm-up)."""
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = Solver.from_workload(w, stream=stream, precision=precision)
+        fields = [torch.from_numpy(x).to("cuda") for x in (w.rho, w.ux, w.uy, w.T)]
+        s.init(*fields)
+        s.step(warmup)
+    s.sync()
+    a0 = tgv_amplitude(w, s.macros()[1])
+    torch.cuda.synchronize()
+    return s, stream, a0
+
+
 def run_cdbm(a, rank, world, local_rank):
     import numpy as np
     import torch
     import torch.distributed as dist
 
-    from paper_2502_16818_gb300 import Solver, cdbm
+    from paper_2502_16818_gb300 import CDBM_FP32_BULK, CDBM_FP64, Solver, cdbm
 
     torch.cuda.set_device(local_rank)
     w = workload(a.n)
     cells = w.nx * w.ny
-    stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        s = Solver.from_workload(w, stream=stream)
-        fields = [torch.from_numpy(x).to("cuda", non_blocking=False) for x in (w.rho, w.ux, w.uy, w.T)]
-        s.init(*fields)
-        s.step(a.warmup)
-    s.sync()
-    torch.cuda.synchronize()
+    s, stream, amp0 = time_tgv(w, CDBM_FP64, a.steps, a.warmup, torch, Solver)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -221,6 +239,11 @@ def run_cdbm(a, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
     value = cells * a.steps * world / (ms_max * 1e-3)
+    rho64, ux64, _, T64 = s.macros()
+    amp1 = tgv_amplitude(w, ux64)
+    t_run = a.steps * w.dt
+    nu = float(T64.mean()) * w.tau
+    decay = {"measured": -np.log(amp1 / amp0) / t_run, "navier_stokes": 2 * nu * w.extra["k"] ** 2}
 
     # roofline of the dominant kernels (the two fused stage kernels, ~100% of the step)
     launch_ms = ms / (2 * a.steps)
@@ -233,7 +256,7 @@ def run_cdbm(a, rank, world, local_rank):
     traffic = TRAFFIC_BYTES_PER_LAUNCH if TRAFFIC_SHA == kernel_sha() else None
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved_tflops / peak_tflops, "traffic": traffic,
-                "kernel": "stage_kernel (RK stages 1 and 2, mean per launch)",
+                "kernel": "stage_march_kernel (RK stages 1 and 2, mean per launch)",
                 "peak_source": "FP64 pipe: 2 lanes/clk/SM x 152 SMs x 2070 MHz x 2 flops (recipe nominal 1.25 TFLOP/s)",
                 "fp64_pipe_frac": instr_rate / peak_instr,
                 "hbm_gbs": hbm_gbs, "hbm_frac_of_measured": hbm_gbs / measured_hbm()}
@@ -249,15 +272,96 @@ def run_cdbm(a, rank, world, local_rank):
         "gpu_launches": 2 * a.steps,
         "clocks": clocks,
         "roofline": roofline,
+        "decay_rate": decay,
     }
 
     if not a.no_e2e:
         out["e2e"] = e2e(a, w, stream, cdbm, s, torch)
     s.close()
+
+    if not a.no_variants and rank == 0:
+        out["fp32_bulk"] = fp32_variant(a, w, torch, Solver, CDBM_FP32_BULK, rho64, value, amp0)
+        out["ensemble"] = ensemble(a, torch)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+def fp32_variant(a, w, torch, Solver, precision, rho64, value64, amp0):
+    """The FP32-bulk state on the same vortex and steps: throughput, speed-up over the
+    FP64 plain path, relative L2 density error against the FP64 run, decay rate."""
+    import numpy as np
+    s, stream, _ = time_tgv(w, precision, a.steps, a.warmup, torch, Solver)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(a.steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    s.sync()
+    rho, ux, _, T = s.macros()
+    s.close()
+    l2 = float(torch.linalg.norm(rho - rho64) / torch.linalg.norm(rho64))
+    val = w.nx * w.ny * a.steps / (ms * 1e-3)
+    amp1 = tgv_amplitude(w, ux)
+    return {"value": val, "unit": UNIT, "ms_per_step": ms / a.steps, "speedup_vs_fp64": val / value64,
+            "l2_density_error_vs_fp64": l2, "steps_compared": a.steps + a.warmup,
+            "decay_rate_measured": float(-np.log(amp1 / amp0) / (a.steps * w.dt)),
+            "hbm_gbs": 320 * w.nx * w.ny * a.steps / (ms * 1e-3) / 1e9,
+            "note": "f in single precision as deviation from a reference equilibrium; sums, "
+                    "moment shift and equilibrium product in double"}
+
+
+def ensemble(a, torch):
+    """1024 shock tubes, Nx ~ U{200..4000} (seed 0), one persistent autotuned launch
+    per call, FP64 and FP32-bulk; against a per-tube loop of the single-grid FP64
+    solver over the same tubes."""
+    from paper_2502_16818_gb300 import BatchSolver, Solver, workloads as W
+    specs = W.ensemble_draw(1024, seed=0)
+    tubes = [W.ensemble_tube(sp, steps=1000) for sp in specs]
+    res = {"tubes": len(tubes), "cells": int(sum(w.nx for w in tubes)), "steps": a.ens_steps}
+    for name, prec in (("fp64_batched", 0), ("fp32_bulk_batched", 1)):
+        st = torch.cuda.Stream()
+        b = BatchSolver(tubes, precision=prec, stream=st)
+        b.init(tubes)
+        tile = b.autotune(5)
+        b.step(3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        b.step(a.ens_steps)
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        b.sync()
+        b.close()
+        res[name] = {"value": res["cells"] * a.ens_steps / (ms * 1e-3), "unit": UNIT, "tile": tile,
+                     "gpu_launches": 1}
+    # per-tube loop: one single-grid FP64 solver per tube, stepped one after another
+    st = torch.cuda.Stream()
+    solvers = []
+    for w in tubes:
+        s = Solver.from_workload(w, stream=st)
+        s.init(w.rho, w.ux, w.uy, w.T)
+        solvers.append(s)
+    loop_steps = 32
+    for s in solvers:
+        s.step(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for s in solvers:
+        s.step(loop_steps)
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    for s in solvers:
+        s.sync()
+        s.close()
+    res["fp64_per_tube_loop"] = {"value": res["cells"] * loop_steps / (ms * 1e-3), "unit": UNIT,
+                                 "steps": loop_steps, "gpu_launches": 2 * loop_steps * len(tubes)}
+    res["batched_fp32_vs_fp64_plain_loop"] = res["fp32_bulk_batched"]["value"] / res["fp64_per_tube_loop"]["value"]
+    return res
 
 
 def e2e(a, w, stream, cdbm, s, torch):
