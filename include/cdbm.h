@@ -170,6 +170,36 @@ cdbm_status cdbm_state_ptr(cdbm_ctx *ctx, void **f);
 /* Simulated time (host scalar). */
 cdbm_status cdbm_time(const cdbm_ctx *ctx, double *t);
 
+/* ------------------------------------------------------------------------------
+ * Adjoint (reverse mode) of the time step, for gradients of a loss of the final
+ * state with respect to the initial fields and tau.  Requires CDBM_FP64,
+ * CDBM_RK2_TVD and periodic boundaries on every axis with more than one cell.
+ * The limiter enters through its subgradient: the derivative of the branch the
+ * forward pass took (1 for the argument minmod returned, 0 for the other, 0 when it
+ * returned 0).  Pointers are device pointers.
+ * ---------------------------------------------------------------------------- */
+
+/* Runs nsteps >= 1 steps like cdbm_step from the current state and records a
+ * checkpoint of the state every `every` steps (ceil(nsteps / every) states of
+ * [16][ny][nx] doubles, allocated through the context allocator).  The run must be
+ * the last thing done to the state before cdbm_adjoint_backward. */
+cdbm_status cdbm_adjoint_forward(cdbm_ctx *ctx, int nsteps, int every);
+
+/* Given fbar = dL/df of the state at the end of the recorded run ([16][ny][nx]),
+ * writes dL/drho0, dL/du_x0, dL/du_y0, dL/dT0 of the fields the state was
+ * initialised from by cdbm_init ([ny][nx] each; NULL skips) and dL/dtau (host
+ * scalar; NULL skips).  Each segment between checkpoints is recomputed forward
+ * (min(every, nsteps) states held at once), then swept backward through the
+ * transposed stages.  Synchronous.  Errors: CDBM_EINVAL without a recorded run that
+ * ends at the current state; CDBM_ENOMEM. */
+cdbm_status cdbm_adjoint_backward(cdbm_ctx *ctx, const double *fbar, double *grad_rho, double *grad_ux,
+                                  double *grad_uy, double *grad_T, double *grad_tau);
+
+/* fbar = (d(rho, u_x, u_y, T)/df)^T (rho_bar, ux_bar, uy_bar, T_bar) at the current
+ * state (the read-out of cdbm_macros transposed); NULL cotangents count as zero. */
+cdbm_status cdbm_macros_vjp(cdbm_ctx *ctx, const double *rho_bar, const double *ux_bar, const double *uy_bar,
+                            const double *T_bar, double *fbar);
+
 /* Waits for the context stream and reports a sticky CUDA error or the
  * device-side non-physical flag (CDBM_ENONPHYS). */
 cdbm_status cdbm_sync(cdbm_ctx *ctx);

@@ -29,7 +29,8 @@ EXPORTS = ("cdbm_create", "cdbm_set_rk", "cdbm_init", "cdbm_step", "cdbm_macros"
            "cdbm_sync", "cdbm_last_error", "cdbm_destroy", "cdbm_step_noalloc",
            "cdbm_batch_create", "cdbm_batch_init", "cdbm_batch_step", "cdbm_batch_autotune",
            "cdbm_batch_set_tile", "cdbm_batch_macros", "cdbm_batch_info", "cdbm_batch_sync",
-           "cdbm_batch_last_error", "cdbm_batch_destroy")
+           "cdbm_batch_last_error", "cdbm_batch_destroy", "cdbm_adjoint_forward",
+           "cdbm_adjoint_backward", "cdbm_macros_vjp")
 CDBM_NOALLOC_MAX_CELLS = 32768
 
 
@@ -108,6 +109,9 @@ def load(path: str | None = None):
         "cdbm_batch_sync": ([ctx], ctypes.c_int),
         "cdbm_batch_last_error": ([ctx], ctypes.c_char_p),
         "cdbm_batch_destroy": ([ctx], None),
+        "cdbm_adjoint_forward": ([ctx, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "cdbm_adjoint_backward": ([ctx, _vp, _vp, _vp, _vp, _vp, _dp], ctypes.c_int),
+        "cdbm_macros_vjp": ([ctx, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -213,6 +217,26 @@ def cdbm_step_noalloc(grid: cdbm_grid, vset: cdbm_vset, I, tau, dt, f, nsteps, s
     st = lib.cdbm_step_noalloc(ctypes.byref(grid), ctypes.byref(vset), float(I), float(tau),
                                float(dt), ctypes.c_void_p(f), int(nsteps), ctypes.c_void_p(stream))
     _check(lib, None, st)
+
+
+def cdbm_adjoint_forward(ctx, nsteps, every):
+    lib = load()
+    _check(lib, ctx, lib.cdbm_adjoint_forward(ctx, int(nsteps), int(every)))
+
+
+def cdbm_adjoint_backward(ctx, fbar, grad_rho=0, grad_ux=0, grad_uy=0, grad_T=0):
+    """Device addresses in, dL/dtau out (float)."""
+    lib = load()
+    gt = ctypes.c_double()
+    _check(lib, ctx, lib.cdbm_adjoint_backward(ctx, fbar, grad_rho or None, grad_ux or None, grad_uy or None,
+                                               grad_T or None, ctypes.byref(gt)))
+    return gt.value
+
+
+def cdbm_macros_vjp(ctx, rho_bar, ux_bar, uy_bar, T_bar, fbar):
+    lib = load()
+    _check(lib, ctx, lib.cdbm_macros_vjp(ctx, rho_bar or None, ux_bar or None, uy_bar or None, T_bar or None,
+                                         fbar))
 
 
 def _bcheck(lib, b, status):
@@ -475,3 +499,43 @@ class BatchSolver:
             self.close()
         except Exception:
             pass
+
+
+def make_run_function():
+    """torch.autograd.Function over a whole CDBM run (built lazily so that importing
+    this module does not import torch)."""
+    import torch
+
+    class CDBMRun(torch.autograd.Function):
+        """(rho, u_x, u_y, T) at the end of `nsteps` steps from initial fields
+        (rho0, ux0, uy0, T0) and relaxation time tau; `spec` holds the remaining run
+        parameters (nx, ny, dx, dy, dt, I, vg, eg; periodic axes).  The backward pass
+        runs the adjoint kernels with a checkpoint every `every` steps."""
+
+        @staticmethod
+        def forward(ctx, rho0, ux0, uy0, T0, tau, spec, nsteps, every):
+            s = Solver(spec["nx"], spec["ny"], spec["dx"], spec["dy"], spec["dt"], float(tau), spec["I"],
+                       spec["vg"], spec["eg"])
+            s.init(rho0.detach(), ux0.detach(), uy0.detach(), T0.detach())
+            cdbm_adjoint_forward(s.ctx, nsteps, every)
+            out = s.macros()
+            ctx.solver = s
+            ctx.tau_like = tau
+            return out
+
+        @staticmethod
+        def backward(ctx, grho, gux, guy, gT):
+            s = ctx.solver
+            dev = s.device
+            ptr = lambda g: g.contiguous().data_ptr() if g is not None else 0
+            keep = [g.contiguous() if g is not None else None for g in (grho, gux, guy, gT)]
+            fbar = torch.empty((16, s.ny, s.nx), dtype=torch.float64, device=dev)
+            cdbm_macros_vjp(s.ctx, *(ptr(g) for g in keep), fbar.data_ptr())
+            grads = [torch.empty((s.ny, s.nx), dtype=torch.float64, device=dev) for _ in range(4)]
+            gtau = cdbm_adjoint_backward(s.ctx, fbar.data_ptr(), *(g.data_ptr() for g in grads))
+            s.close()
+            tau = ctx.tau_like
+            gtau_t = torch.tensor(gtau, dtype=tau.dtype, device=tau.device) if torch.is_tensor(tau) else None
+            return grads[0], grads[1], grads[2], grads[3], gtau_t, None, None, None
+
+    return CDBMRun

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "../../include/cdbm.h"
 #include "cdbm_device.cuh"
@@ -70,6 +71,12 @@ struct cdbm_ctx {
     FieldArgs fields;
 
     cudaGraphExec_t graph;
+
+    // adjoint record of the last cdbm_adjoint_forward
+    int adj_steps, adj_every;     // steps recorded, checkpoint interval (0: none)
+    long long step_count;         // steps taken since the state was set
+    long long adj_end;            // step_count at the end of the recorded run
+    std::vector<void *> ckpt;     // states at steps 0, k, 2k, ... of the recorded run
 
     cdbm_status err;
     char msg[256];
@@ -548,6 +555,8 @@ cdbm_status cdbm_init(cdbm_ctx *c, const double *rho, const double *ux, const do
     if (any_host && cuda_check(c, cudaStreamSynchronize(c->stream), "cdbm_init sync")) return c->err;
     c->t = 0.0;
     c->state_set = true;
+    c->step_count = 0;
+    c->adj_steps = 0;
     return CDBM_OK;
 }
 
@@ -566,6 +575,7 @@ cdbm_status cdbm_step(cdbm_ctx *c, int nsteps)
     for (; left > 0; --left)
         if (enqueue_step(c)) return c->err;
     c->t += nsteps * c->dt;
+    c->step_count += nsteps;
     return CDBM_OK;
 }
 
@@ -691,6 +701,8 @@ cdbm_status cdbm_set_state(cdbm_ctx *c, const double *f, double t)
     if (host && cuda_check(c, cudaStreamSynchronize(c->stream), "cdbm_set_state sync")) return c->err;
     c->t = t;
     c->state_set = true;
+    c->step_count = 0;
+    c->adj_steps = 0;
     return CDBM_OK;
 }
 
@@ -706,6 +718,134 @@ cdbm_status cdbm_time(const cdbm_ctx *c, double *t)
     if (!c || !t) return CDBM_EINVAL;
     *t = c->t;
     return c->err;
+}
+
+namespace {
+
+cdbm_status adjoint_supported(cdbm_ctx *c, const char *who)
+{
+    if (c->precision != CDBM_FP64) return set_err(c, CDBM_EINVAL, "%s: needs CDBM_FP64", who);
+    if (c->rk != CDBM_RK2_TVD) return set_err(c, CDBM_EINVAL, "%s: needs CDBM_RK2_TVD", who);
+    if ((c->grid.nx > 1 && c->grid.bc_x != CDBM_BC_PERIODIC) || (c->grid.ny > 1 && c->grid.bc_y != CDBM_BC_PERIODIC))
+        return set_err(c, CDBM_EINVAL, "%s: needs periodic boundaries", who);
+    return CDBM_OK;
+}
+
+void free_ckpt(cdbm_ctx *c)
+{
+    for (void *p : c->ckpt) ctx_free(c, p, sizeof(double) * kNV * c->plane);
+    c->ckpt.clear();
+    c->adj_steps = 0;
+}
+
+}  // namespace
+
+cdbm_status cdbm_adjoint_forward(cdbm_ctx *c, int nsteps, int every)
+{
+    if (!c) return CDBM_EINVAL;
+    if (c->err) return c->err;
+    if (adjoint_supported(c, "cdbm_adjoint_forward")) return c->err;
+    if (nsteps < 1 || every < 1) return set_err(c, CDBM_EINVAL, "cdbm_adjoint_forward: nsteps, every >= 1");
+    if (!c->state_set) return set_err(c, CDBM_EINVAL, "cdbm_adjoint_forward: state not initialised");
+    free_ckpt(c);
+    const size_t fb = sizeof(double) * kNV * c->plane;
+    const int nck = (nsteps + every - 1) / every;
+    for (int k = 0; k < nck; ++k) {
+        void *p = ctx_alloc(c, fb);
+        if (!p) {
+            free_ckpt(c);
+            return set_err(c, CDBM_ENOMEM, "checkpoint allocation (%d x %zu bytes) failed", nck, fb);
+        }
+        c->ckpt.push_back(p);
+    }
+    for (int k = 0; k < nck; ++k) {
+        if (cuda_check(c, cudaMemcpyAsync(c->ckpt[k], c->f, fb, cudaMemcpyDeviceToDevice, c->stream), "checkpoint"))
+            return c->err;
+        const int n = (k + 1) * every <= nsteps ? every : nsteps - k * every;
+        if (cdbm_step(c, n)) return c->err;
+    }
+    c->adj_steps = nsteps;
+    c->adj_every = every;
+    c->adj_end = c->step_count;
+    return CDBM_OK;
+}
+
+cdbm_status cdbm_adjoint_backward(cdbm_ctx *c, const double *fbar, double *grad_rho, double *grad_ux,
+                                  double *grad_uy, double *grad_T, double *grad_tau)
+{
+    if (!c) return CDBM_EINVAL;
+    if (c->err) return c->err;
+    if (!fbar) return set_err(c, CDBM_EINVAL, "cdbm_adjoint_backward: NULL cotangent");
+    if (c->adj_steps < 1 || c->step_count != c->adj_end)
+        return set_err(c, CDBM_EINVAL, "cdbm_adjoint_backward: no recorded run ending at the current state");
+    const int nsteps = c->adj_steps, every = c->adj_every;
+    const size_t n = kNV * c->plane, fb = sizeof(double) * n;
+    const dim3 ag = adjoint_grid(c->grid.nx, c->grid.ny);
+    const int nacc = (int)(ag.x * ag.y);
+    const int seglen = every < nsteps ? every : nsteps;
+    // B: cotangent of the current state; B1: of the stage-1 state; G1: stage-1 state;
+    // seg: the states of one segment, recomputed from its checkpoint
+    std::vector<void *> bufs;
+    auto grab = [&](size_t bytes) {
+        void *p = ctx_alloc(c, bytes);
+        bufs.push_back(p);
+        return (double *)p;
+    };
+    double *B = grab(fb), *B1 = grab(fb), *G1 = grab(fb);
+    double *acc = grab(sizeof(double) * (nacc + 1));
+    std::vector<double *> seg(seglen);
+    for (int j = 1; j < seglen; ++j) seg[j] = grab(fb);
+    bool ok = true;
+    for (void *p : bufs) ok = ok && p;
+    cdbm_status st = CDBM_OK;
+    if (!ok) st = set_err(c, CDBM_ENOMEM, "adjoint work buffers (%d states) failed", seglen + 2);
+    const double h = c->dt / c->tau, inv_tau = 1.0 / c->tau;
+    if (!st && (cuda_check(c, cudaMemcpyAsync(B, fbar, fb, cudaMemcpyDefault, c->stream), "cotangent copy") ||
+                cuda_check(c, cudaMemsetAsync(acc, 0, sizeof(double) * (nacc + 1), c->stream), "acc clear")))
+        st = c->err;
+    const int nseg = (nsteps + every - 1) / every;
+    for (int sgi = nseg - 1; sgi >= 0 && !st; --sgi) {
+        const int len = (sgi + 1) * every <= nsteps ? every : nsteps - sgi * every;
+        seg[0] = (double *)c->ckpt[sgi];
+        for (int j = 0; j + 1 < len && !st; ++j) {
+            cudaError_t e = launch_stage(c->launch[0], seg[j], nullptr, G1, c->stage[0], c->flag, c->stream);
+            if (e == cudaSuccess)
+                e = launch_stage(c->launch[1], G1, seg[j], seg[j + 1], c->stage[1], c->flag, c->stream);
+            st = cuda_check(c, e, "adjoint recompute");
+        }
+        for (int j = len - 1; j >= 0 && !st; --j) {
+            cudaError_t e = launch_stage(c->launch[0], seg[j], nullptr, G1, c->stage[0], c->flag, c->stream);
+            if (e == cudaSuccess)   // stage 2: f^{n+1} = f^n/2 + f1/2 + dt/2 L(f1)
+                e = launch_adjoint_stage(G1, B, nullptr, 0.0, B1, c->stage[1], 0.5 * h, inv_tau, acc, c->stream);
+            if (e == cudaSuccess)   // stage 1: f1 = f^n + dt L(f^n); plus the f^n/2 of stage 2
+                e = launch_adjoint_stage(seg[j], B1, B, 0.5, B, c->stage[0], h, inv_tau, acc, c->stream);
+            st = cuda_check(c, e, "adjoint stage");
+        }
+    }
+    if (!st && cuda_check(c, launch_init_vjp(c->fields, (const double *)c->ckpt[0], B, grad_rho, grad_ux, grad_uy,
+                                             grad_T, c->stream), "init vjp"))
+        st = c->err;
+    if (!st && grad_tau) {
+        if (cuda_check(c, launch_sum(acc, nacc, acc + nacc, c->stream), "tau sum") ||
+            cuda_check(c, cudaMemcpyAsync(grad_tau, acc + nacc, sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                       "tau download"))
+            st = c->err;
+    }
+    if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "adjoint sync");
+    for (size_t k = 0; k < bufs.size(); ++k) ctx_free(c, bufs[k], k == 3 ? sizeof(double) * (nacc + 1) : fb);
+    return st;
+}
+
+cdbm_status cdbm_macros_vjp(cdbm_ctx *c, const double *rho_bar, const double *ux_bar, const double *uy_bar,
+                            const double *T_bar, double *fbar)
+{
+    if (!c) return CDBM_EINVAL;
+    if (c->err) return c->err;
+    if (!fbar) return set_err(c, CDBM_EINVAL, "cdbm_macros_vjp: NULL output");
+    if (c->precision != CDBM_FP64) return set_err(c, CDBM_EINVAL, "cdbm_macros_vjp: needs CDBM_FP64");
+    if (!c->state_set) return set_err(c, CDBM_EINVAL, "cdbm_macros_vjp: state not initialised");
+    return cuda_check(c, launch_macros_vjp(c->fields, (const double *)c->f, rho_bar, ux_bar, uy_bar, T_bar, fbar,
+                                           c->stream), "macros vjp");
 }
 
 cdbm_status cdbm_sync(cdbm_ctx *c)
@@ -731,6 +871,8 @@ void cdbm_destroy(cdbm_ctx *c)
 {
     if (!c) return;
     drop_graph(c);
+    for (void *p : c->ckpt) ctx_free(c, p, sizeof(double) * kNV * c->plane);
+    c->ckpt.clear();
     ctx_free(c, c->f, storage_bytes(c->precision) * kNV * c->plane);
     ctx_free(c, c->f1, sizeof(double) * kNV * c->plane);
     ctx_free(c, c->partials, sizeof(double) * 4 * c->sum_blocks + sizeof(double) * 4 + 256);

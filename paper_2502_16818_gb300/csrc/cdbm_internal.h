@@ -121,6 +121,18 @@ StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count
 cudaError_t launch_stage(const StageLaunch &L, const void *g, const void *base, void *out,
                          const StageArgs &a, unsigned *flag, cudaStream_t s);
 
+// ---- adjoint kernels (cdbm_adjoint.cu), double precision, periodic axes ----
+// out_bar = c_prev * prev + (stage VJP at g applied to ob); tau_acc[block] += tau term.
+cudaError_t launch_adjoint_stage(const double *g, const double *ob, const double *prev, double c_prev,
+                                 double *out_bar, const StageArgs &a, double gamma_h, double inv_tau,
+                                 double *tau_acc, cudaStream_t s);
+dim3 adjoint_grid(int nx, int ny);
+cudaError_t launch_init_vjp(const FieldArgs &a, const double *f0, const double *fbar, double *rho_bar,
+                            double *ux_bar, double *uy_bar, double *T_bar, cudaStream_t s);
+cudaError_t launch_macros_vjp(const FieldArgs &a, const double *f, const double *rho_bar, const double *ux_bar,
+                              const double *uy_bar, const double *T_bar, double *fbar, cudaStream_t s);
+cudaError_t launch_sum(const double *v, int n, double *out, cudaStream_t s);
+
 // Bytes of one distribution value in storage precision `prec`.
 inline size_t storage_bytes(int prec) { return prec == CDBM_FP32_BULK ? 4 : 8; }
 

@@ -207,3 +207,28 @@ def ensemble_tube(spec: dict, steps: int = 1000, dt: float = 2e-5, tau: float = 
     """One tube of the ensemble on [0, 1], interface 0.5, Sod velocity set."""
     return _riemann("tube", spec["nx"], 0.0, 1.0, 0.5, (spec["rho"][0], 0.0, spec["T"][0]),
                     (spec["rho"][1], 0.0, spec["T"][1]), dt, tau, spec["I"], VSET_SOD, steps)
+
+
+def sound_modes(n: int = 1024, seed: int = 0, kmax: int = 8, amp: float = 1e-3, I: float = 3.0,
+                steps: int = 4000, dt: float = 2e-5, tau: float = 1e-4) -> Workload:
+    """Periodic unit square with rho and T each perturbed by every Fourier mode
+    (kx, ky) in [0..kmax]^2 with 0 < |k| <= kmax, amplitude amp and a uniform random
+    phase per mode and field (drawn in the order rho modes, then T modes); u = 0.
+    Sound-wave velocity set."""
+    rng = np.random.default_rng(seed)
+    x = _centres(n, 1.0 / n)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    modes = [(kx, ky) for kx in range(kmax + 1) for ky in range(kmax + 1)
+             if 0 < kx * kx + ky * ky <= kmax * kmax]
+    out = []
+    for _ in range(2):
+        a = np.ones((n, n))
+        ph = rng.uniform(0.0, 2.0 * np.pi, len(modes))
+        for (kx, ky), p in zip(modes, ph):
+            a += amp * np.cos(2.0 * np.pi * (kx * X + ky * Y) + p)
+        out.append(a)
+    rho, T = out
+    z = np.zeros((n, n))
+    return Workload(name="sound_modes", nx=n, ny=n, dx=1.0 / n, dy=1.0 / n, dt=dt, tau=tau, I=float(I),
+                    vg=VSET_SOUND[0], eg=VSET_SOUND[1], bc_x=PERIODIC, bc_y=PERIODIC, steps=steps,
+                    rho=rho, ux=z, uy=z.copy(), T=T, extra={"seed": seed, "kmax": kmax, "amp": amp})

@@ -1,0 +1,175 @@
+"""Adjoint of the time step (cdbm_adjoint_*), checked against central finite
+differences: of the GPU forward run (fast, many directions) and of the CPU oracle's
+forward model (independent of every GPU kernel).
+
+Loss: L = sum over cells of (rho_T - rho_target)^2 on a periodic grid whose initial
+rho and T carry seeded Fourier modes (|k| <= kmax, amplitude 1e-3), u = 0.  The
+directional derivative of L along smooth unit-scale directions of rho0 and T0 must
+agree with central differences to 3e-5 relative, and dL/dtau to 5e-4.
+
+Why these bounds: the scheme is only piecewise smooth (minmod), so a central
+difference of step h carries an O(h) error from the cells whose limiter branch
+flips inside +-h, on top of the O(eps L / h) rounding error.  Measured on this
+case, the relative gap between adjoint and difference falls from 4.8e-4 (h = 1e-4)
+through 1.3e-4, 8e-6, 1.7e-6 to 6e-8 (h = 1e-8) along one direction; for tau the
+best step, 1e-3 tau, leaves 5e-5, while 1e-6 tau is already dominated by rounding.
+Along a velocity direction (a 40x smaller derivative) the gap grows as h shrinks
+below 1e-6 (1.1e-6 at h = 1e-6, 8e-5 at 1e-9): rounding, so that test uses 1e-6.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_16818_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL = 3e-5
+RTOL_TAU = 5e-4
+H = 1e-7
+H_TAU = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_16818_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+
+
+def spec_of(w):
+    return {"nx": w.nx, "ny": w.ny, "dx": w.dx, "dy": w.dy, "dt": w.dt, "I": w.I, "vg": w.vg, "eg": w.eg}
+
+
+def setup(n=48, steps=120, every=25, seed=11, kmax=4):
+    w = W.sound_modes(n=n, seed=seed, kmax=kmax, steps=steps)
+    target = W.sound_modes(n=n, seed=seed + 1, kmax=kmax).rho
+    return w, target, steps, every
+
+
+def gpu_loss(w, rho0, T0, tau, target, steps):
+    from paper_2502_16818_gb300 import Solver
+    s = Solver(w.nx, w.ny, w.dx, w.dy, w.dt, tau, w.I, w.vg, w.eg)
+    s.init(rho0, w.ux, w.uy, T0)
+    s.step(steps)
+    rho = s.macros()[0].cpu().numpy()
+    s.close()
+    return float(np.sum((rho - target) ** 2))
+
+
+def oracle_loss(w, rho0, T0, tau, target, steps):
+    m = oracle.Model(nx=w.nx, ny=w.ny, dx=w.dx, dy=w.dy, dt=w.dt, tau=tau, I=w.I, vg=w.vg, eg=w.eg)
+    f = oracle.step(m, oracle.init(m, rho0, w.ux, w.uy, T0), steps)
+    rho = oracle.macros(m, f)[0]
+    return float(np.sum((rho - target) ** 2))
+
+
+def adjoint_grads(w, target, steps, every):
+    """(dL/drho0, dL/dT0, dL/dtau) through the autograd Function."""
+    from paper_2502_16818_gb300.cdbm import make_run_function
+    Run = make_run_function()
+    dev = "cuda"
+    rho0 = torch.tensor(w.rho, device=dev, requires_grad=True)
+    T0 = torch.tensor(w.T, device=dev, requires_grad=True)
+    ux0 = torch.tensor(w.ux, device=dev, requires_grad=True)
+    uy0 = torch.tensor(w.uy, device=dev, requires_grad=True)
+    tau = torch.tensor(w.tau, dtype=torch.float64, requires_grad=True)
+    rho, ux, uy, T = Run.apply(rho0, ux0, uy0, T0, tau, spec_of(w), steps, every)
+    loss = ((rho - torch.tensor(target, device=dev)) ** 2).sum()
+    loss.backward()
+    return (rho0.grad.cpu().numpy(), T0.grad.cpu().numpy(), float(tau.grad), float(loss.detach()),
+            ux0.grad.cpu().numpy())
+
+
+def direction(n, seed, kmax=4):
+    """A smooth unit-amplitude direction (seeded Fourier modes): smooth perturbations
+    leave the limiter's branch pattern unchanged, unlike grid-scale noise."""
+    return (W.sound_modes(n=n, seed=seed, kmax=kmax, amp=1.0).rho - 1.0) / 8.0
+
+
+def central(fn, h):
+    return (fn(h) - fn(-h)) / (2 * h)
+
+
+@pytest.fixture(scope="module")
+def case():
+    w, target, steps, every = setup()
+    return w, target, steps, every, adjoint_grads(w, target, steps, every)
+
+
+def test_loss_matches_forward(case):
+    w, target, steps, every, (gr, gT, gtau, loss, _) = case
+    assert loss == pytest.approx(gpu_loss(w, w.rho, w.T, w.tau, target, steps), rel=1e-14)
+
+
+def test_directional_derivatives_vs_gpu_fd(case):
+    w, target, steps, every, (gr, gT, gtau, loss, _) = case
+    for k in range(6):
+        dr, dT = direction(w.nx, 100 + k), direction(w.nx, 200 + k)
+        ad = float(np.sum(gr * dr) + np.sum(gT * dT))
+        fd = central(lambda e: gpu_loss(w, w.rho + e * dr, w.T + e * dT, w.tau, target, steps), H)
+        assert ad == pytest.approx(fd, rel=RTOL), (k, ad, fd)
+    fd = central(lambda e: gpu_loss(w, w.rho, w.T, w.tau + e, target, steps), H_TAU * w.tau)
+    assert gtau == pytest.approx(fd, rel=RTOL_TAU), (gtau, fd)
+
+
+def test_directional_derivatives_vs_oracle_fd(case):
+    """Central differences of the CPU oracle's forward model, which shares no code
+    with the adjoint kernels."""
+    w, target, steps, every, (gr, gT, gtau, loss, _) = case
+    for k in range(2):
+        dr, dT = direction(w.nx, 300 + k), direction(w.nx, 400 + k)
+        ad = float(np.sum(gr * dr) + np.sum(gT * dT))
+        fd = central(lambda e: oracle_loss(w, w.rho + e * dr, w.T + e * dT, w.tau, target, steps), H)
+        assert ad == pytest.approx(fd, rel=RTOL), (k, ad, fd)
+    fd = central(lambda e: oracle_loss(w, w.rho, w.T, w.tau + e, target, steps), H_TAU * w.tau)
+    assert gtau == pytest.approx(fd, rel=RTOL_TAU), (gtau, fd)
+
+
+def test_velocity_gradient_vs_gpu_fd(case):
+    from paper_2502_16818_gb300 import Solver
+    w, target, steps, every, (gr, gT, gtau, loss, gux) = case
+    du = direction(w.nx, 500)
+
+    def L(e):
+        s = Solver(w.nx, w.ny, w.dx, w.dy, w.dt, w.tau, w.I, w.vg, w.eg)
+        s.init(w.rho, w.ux + e * du, w.uy, w.T)
+        s.step(steps)
+        rho = s.macros()[0].cpu().numpy()
+        s.close()
+        return float(np.sum((rho - target) ** 2))
+    fd = central(L, 10 * H)     # a derivative 40x smaller than the density one: rounding sets the step
+    assert float(np.sum(gux * du)) == pytest.approx(fd, rel=RTOL)
+
+
+def test_checkpoint_interval_does_not_change_gradients():
+    w, target, steps, every = setup(n=32, steps=40)
+    a = adjoint_grads(w, target, steps, 40)
+    b = adjoint_grads(w, target, steps, 7)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2]
+
+
+def test_flux_only_adjoint():
+    """With tau large the collision term is tiny: the gradient is carried by the
+    transposed NND transport and its limiter subgradient."""
+    w, target, steps, every = setup(n=32, steps=60, seed=5)
+    w.tau = 1e3
+    gr, gT, gtau, loss, _ = adjoint_grads(w, target, steps, every)
+    dr = direction(w.nx, 600)
+    fd = central(lambda e: gpu_loss(w, w.rho + e * dr, w.T, w.tau, target, steps), H)
+    assert float(np.sum(gr * dr)) == pytest.approx(fd, rel=RTOL)
+
+
+def test_adjoint_requires_periodic_fp64():
+    from paper_2502_16818_gb300 import CdbmError, Solver, cdbm
+    w = W.sod(nx=50)
+    s = Solver.from_workload(w)
+    s.init(w.rho, w.ux, w.uy, w.T)
+    with pytest.raises(CdbmError, match="periodic"):
+        cdbm.cdbm_adjoint_forward(s.ctx, 10, 5)
+    s.close()
