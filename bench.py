@@ -212,7 +212,7 @@ def run_cdbm(a, rank, world, local_rank):
     import torch
     import torch.distributed as dist
 
-    from paper_2502_16818_gb300 import CDBM_FP32_BULK, CDBM_FP64, Solver, cdbm
+    from paper_2502_16818_gb300 import CDBM_FP32_BULK, CDBM_FP64, Solver, cdbm, replicas
 
     torch.cuda.set_device(local_rank)
     w = workload(a.n)
@@ -233,12 +233,10 @@ def run_cdbm(a, rank, world, local_rank):
     ms = e0.elapsed_time(e1)
     s.sync()
     torch.cuda.synchronize()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.barrier()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = cells * a.steps * world / (ms_max * 1e-3)
+    ms_max = replicas.max_over_ranks(ms, device="cuda")
+    value = replicas.job_throughput(cells * a.steps, world, ms_max * 1e-3)
     rho64, ux64, _, T64 = s.macros()
     amp1 = tgv_amplitude(w, ux64)
     t_run = a.steps * w.dt
