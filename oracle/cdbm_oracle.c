@@ -285,10 +285,14 @@ static int ghost_index(int j, int n, int bc)
     return j < 0 ? 0 : (j >= n ? n - 1 : j);
 }
 
+/* threads > 0 sets the OpenMP thread count for this call; 0 restores the count the
+ * runtime started with (omp_set_num_threads would otherwise stick). */
 static void set_threads(const orc_params *p)
 {
 #ifdef _OPENMP
-    if (p->threads > 0) omp_set_num_threads(p->threads);
+    static int default_threads = 0;
+    if (default_threads == 0) default_threads = omp_get_max_threads();
+    omp_set_num_threads(p->threads > 0 ? p->threads : default_threads);
 #else
     (void)p;
 #endif
