@@ -232,3 +232,32 @@ def sound_modes(n: int = 1024, seed: int = 0, kmax: int = 8, amp: float = 1e-3, 
     return Workload(name="sound_modes", nx=n, ny=n, dx=1.0 / n, dy=1.0 / n, dt=dt, tau=tau, I=float(I),
                     vg=VSET_SOUND[0], eg=VSET_SOUND[1], bc_x=PERIODIC, bc_y=PERIODIC, steps=steps,
                     rho=rho, ux=z, uy=z.copy(), T=T, extra={"seed": seed, "kmax": kmax, "amp": amp})
+
+
+def paper_sod(steps: int = 400) -> Workload:
+    """Sec. 3.1 as printed: 1500 x 1 cells on [0, 0.15] (dx = 1e-4), interface 0.075,
+    dt = 2e-5, tau = 1e-4, gamma = 2 (I = 0)."""
+    return _riemann("paper_sod", 1500, 0.0, 0.15, 0.075, (1.0, 0.0, 1.0), (0.125, 0.0, 0.8),
+                    2e-5, 1e-4, 0.0, VSET_SOD, steps)
+
+
+def paper_lax(steps: int = 10000) -> Workload:
+    """Sec. 3.2 as printed: 1000 x 1 cells on [0, 2] (dx = 2e-3), interface 1, dt = 2e-5,
+    tau = 1e-4, gamma = 1.4 (I = 3), t = 0.2."""
+    return _riemann("paper_lax", 1000, 0.0, 2.0, 1.0, (0.445, 0.698, 7.928), (0.5, 0.0, 1.142),
+                    2e-5, 1e-4, 3.0, VSET_LAX, steps)
+
+
+def paper_shock(steps: int = 20000, tau: float = 1e-5) -> Workload:
+    """Sec. 3.3: Ma = 15 shock into (1, 0, 1), post-shock state (5.8696, 14.7245, 44.6938)
+    for x <= 0.02; 10000 x 1 cells with dx = 2e-4 (so the domain is [0, 2]; the text's
+    x <= 1.5 does not match 10000 dx), dt = 2e-6, gamma = 1.4 (I = 3).  The paper
+    gives no tau; 1e-5 keeps dt / tau = 0.2."""
+    return _riemann("paper_shock", 10000, 0.0, 2.0, 0.02, (5.8696, 14.7245, 44.6938), (1.0, 0.0, 1.0),
+                    2e-6, tau, 3.0, VSET_SHOCK, steps)
+
+
+def paper_taylor_green(n: int, dt: float = 2e-5, tau: float = 5e-4) -> Workload:
+    """Sec. 3.5: the vortex on [0, 0.1]^2 with tau = 5e-4, gamma = 1.4, velocity set
+    (0.2, 0.2, 2, 2) / (0, 5, 0, 2.6) on an n x n grid."""
+    return taylor_green(n=n, I=3.0, dt=dt, tau=tau)
