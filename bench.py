@@ -75,6 +75,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-variants", action="store_true", help="skip the FP32-bulk and ensemble runs")
     p.add_argument("--ens-steps", type=int, default=200, help="timed steps of the tube ensemble")
+    p.add_argument("--no-ensemble", action="store_true", help="skip the tube ensemble runs")
+    p.add_argument("--adj-steps", type=int, default=4000, help="steps of the adjoint run (0: skip it)")
+    p.add_argument("--adj-every", type=int, default=200, help="checkpoint interval of the adjoint run")
+    p.add_argument("--adj-n", type=int, default=1024, help="grid size of the adjoint run")
     return p.parse_args()
 
 
@@ -212,7 +216,7 @@ def run_cdbm(a, rank, world, local_rank):
     import torch
     import torch.distributed as dist
 
-    from paper_2502_16818_gb300 import CDBM_FP32_BULK, CDBM_FP64, Solver, cdbm, replicas
+    from paper_2502_16818_gb300 import CDBM_FP32_BULK, CDBM_FP32_DF64, CDBM_FP64, Solver, cdbm, replicas
 
     torch.cuda.set_device(local_rank)
     w = workload(a.n)
@@ -278,17 +282,25 @@ def run_cdbm(a, rank, world, local_rank):
     s.close()
 
     if not a.no_variants and rank == 0:
-        out["fp32_bulk"] = fp32_variant(a, w, torch, Solver, CDBM_FP32_BULK, rho64, value, amp0)
-        out["ensemble"] = ensemble(a, torch)
+        out["fp32_bulk"] = fp32_variant(a, w, torch, Solver, CDBM_FP32_BULK, rho64, value, amp0,
+                                        "f in single precision as deviation from a reference "
+                                        "equilibrium; sums, moment shift and equilibrium product in double")
+        out["fp32_df64"] = fp32_variant(a, w, torch, Solver, CDBM_FP32_DF64, rho64, value, amp0,
+                                        "as fp32_bulk, with sums, moment shift and equilibrium product in "
+                                        "double-float arithmetic on the FP32 pipe")
+        if not a.no_ensemble:
+            out["ensemble"] = ensemble(a, torch)
+        if a.adj_steps > 0:
+            out["adjoint"] = adjoint(a, torch)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
         print(json.dumps(out), flush=True)
 
 
-def fp32_variant(a, w, torch, Solver, precision, rho64, value64, amp0):
-    """The FP32-bulk state on the same vortex and steps: throughput, speed-up over the
-    FP64 plain path, relative L2 density error against the FP64 run, decay rate."""
+def fp32_variant(a, w, torch, Solver, precision, rho64, value64, amp0, note):
+    """A single-precision state on the same vortex and steps: throughput, speed-up over
+    the FP64 plain path, relative L2 density error against the FP64 run, decay rate."""
     import numpy as np
     s, stream, _ = time_tgv(w, precision, a.steps, a.warmup, torch, Solver)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -306,20 +318,18 @@ def fp32_variant(a, w, torch, Solver, precision, rho64, value64, amp0):
     return {"value": val, "unit": UNIT, "ms_per_step": ms / a.steps, "speedup_vs_fp64": val / value64,
             "l2_density_error_vs_fp64": l2, "steps_compared": a.steps + a.warmup,
             "decay_rate_measured": float(-np.log(amp1 / amp0) / (a.steps * w.dt)),
-            "hbm_gbs": 320 * w.nx * w.ny * a.steps / (ms * 1e-3) / 1e9,
-            "note": "f in single precision as deviation from a reference equilibrium; sums, "
-                    "moment shift and equilibrium product in double"}
+            "hbm_gbs": 320 * w.nx * w.ny * a.steps / (ms * 1e-3) / 1e9, "note": note}
 
 
 def ensemble(a, torch):
     """1024 shock tubes, Nx ~ U{200..4000} (seed 0), one persistent autotuned launch
-    per call, FP64 and FP32-bulk; against a per-tube loop of the single-grid FP64
-    solver over the same tubes."""
+    per call, FP64, FP32-bulk and FP32 with the df64 equilibrium; against a per-tube
+    loop of the single-grid FP64 solver over the same tubes."""
     from paper_2502_16818_gb300 import BatchSolver, Solver, workloads as W
     specs = W.ensemble_draw(1024, seed=0)
     tubes = [W.ensemble_tube(sp, steps=1000) for sp in specs]
     res = {"tubes": len(tubes), "cells": int(sum(w.nx for w in tubes)), "steps": a.ens_steps}
-    for name, prec in (("fp64_batched", 0), ("fp32_bulk_batched", 1)):
+    for name, prec in (("fp64_batched", 0), ("fp32_bulk_batched", 1), ("fp32_df64_batched", 2)):
         st = torch.cuda.Stream()
         b = BatchSolver(tubes, precision=prec, stream=st)
         b.init(tubes)
@@ -359,7 +369,50 @@ def ensemble(a, torch):
     res["fp64_per_tube_loop"] = {"value": res["cells"] * loop_steps / (ms * 1e-3), "unit": UNIT,
                                  "steps": loop_steps, "gpu_launches": 2 * loop_steps * len(tubes)}
     res["batched_fp32_vs_fp64_plain_loop"] = res["fp32_bulk_batched"]["value"] / res["fp64_per_tube_loop"]["value"]
+    res["batched_df64_vs_fp64_plain_loop"] = res["fp32_df64_batched"]["value"] / res["fp64_per_tube_loop"]["value"]
     return res
+
+
+def adjoint(a, torch):
+    """Gradient of L = sum (rho_T - rho_target)^2 with respect to the initial rho, T
+    (and u) fields and tau on the periodic sound-mode case: forward run storing a
+    checkpoint every `every` steps, then the reverse sweep (segment recomputation
+    and the adjoint stage kernels).  Throughput counts the forward cell-updates over
+    the time of forward plus backward."""
+    from paper_2502_16818_gb300 import Solver, cdbm, workloads as W
+    w = W.sound_modes(n=a.adj_n, seed=0, kmax=8, steps=a.adj_steps)
+    target = torch.from_numpy(W.sound_modes(n=a.adj_n, seed=1, kmax=8).rho).to("cuda")
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        s = Solver.from_workload(w, stream=st)
+        s.init(*(torch.from_numpy(x).to("cuda") for x in (w.rho, w.ux, w.uy, w.T)))
+        grads = [torch.empty((w.ny, w.nx), dtype=torch.float64, device="cuda") for _ in range(4)]
+        fbar = torch.empty((16, w.ny, w.nx), dtype=torch.float64, device="cuda")
+    s.sync()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    t0 = time.perf_counter()
+    ev[0].record(st)
+    cdbm.cdbm_adjoint_forward(s.ctx, a.adj_steps, a.adj_every)
+    ev[1].record(st)
+    with torch.cuda.stream(st):
+        rho = s.macros()[0]
+        grho = 2.0 * (rho - target)
+        loss = float(((rho - target) ** 2).sum())
+    cdbm.cdbm_macros_vjp(s.ctx, grho.data_ptr(), 0, 0, 0, fbar.data_ptr())
+    gtau = cdbm.cdbm_adjoint_backward(s.ctx, fbar.data_ptr(), *(g.data_ptr() for g in grads))
+    ev[2].record(st)
+    ev[2].synchronize()
+    wall = time.perf_counter() - t0
+    fwd_ms, bwd_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    s.close()
+    cells = w.nx * w.ny
+    return {"value": cells * a.adj_steps / ((fwd_ms + bwd_ms) * 1e-3), "unit": UNIT,
+            "workload": "sound_modes_%dx%d_kmax8_fp64" % (w.nx, w.ny), "steps": a.adj_steps,
+            "checkpoint_every": a.adj_every, "forward_ms": fwd_ms, "backward_ms": bwd_ms,
+            "backward_over_forward": bwd_ms / fwd_ms, "wall_s": wall, "loss": loss, "dL_dtau": gtau,
+            "grad_rho_l2": float(torch.linalg.norm(grads[0])), "grad_T_l2": float(torch.linalg.norm(grads[3])),
+            "checkpoint_bytes": 128 * cells * (a.adj_steps // a.adj_every + 1)}
 
 
 def e2e(a, w, stream, cdbm, s, torch):

@@ -85,10 +85,13 @@ typedef struct {
 /* Precision of the stored state. */
 typedef enum {
     CDBM_FP64 = 0,        /* state, flux, equilibrium and sums in IEEE double      */
-    CDBM_FP32_BULK = 1    /* state f and the NND transport in IEEE single; the     */
+    CDBM_FP32_BULK = 1,   /* state f and the NND transport in IEEE single; the     */
                           /* conserved sums, the moment shift and the equilibrium  */
                           /* product in double; f_eq is rounded to single when it  */
                           /* enters the stage update                               */
+    CDBM_FP32_DF64 = 2    /* as CDBM_FP32_BULK, with the sums, moment shift and    */
+                          /* equilibrium product in double-float arithmetic (pairs */
+                          /* of floats, ~48-bit significands) on the FP32 pipe     */
 } cdbm_precision;
 
 /* Time integrator.  The paper names a second-order Runge-Kutta scheme without
@@ -158,13 +161,15 @@ cdbm_status cdbm_tne(cdbm_ctx *ctx, double *out);
 cdbm_status cdbm_conserved_sums(cdbm_ctx *ctx, double out[4]);
 
 /* Copies the state f ([16][ny][nx] doubles, host or device) and the time out / in;
- * a CDBM_FP32_BULK state is widened on the way out and rounded on the way in. */
+ * a single-precision state (CDBM_FP32_BULK, CDBM_FP32_DF64) is widened on the way
+ * out and rounded on the way in. */
 cdbm_status cdbm_get_state(cdbm_ctx *ctx, double *f, double *t);
 cdbm_status cdbm_set_state(cdbm_ctx *ctx, const double *f, double t);
 
 /* Device pointer of the state f ([16][ny][nx], owned by the context, valid until
- * cdbm_destroy; steps update it in place): doubles for CDBM_FP64, floats for
- * CDBM_FP32_BULK. */
+ * cdbm_destroy; steps update it in place): doubles for CDBM_FP64, floats (the
+ * deviation g = f - F from the reference equilibrium F) for CDBM_FP32_BULK and
+ * CDBM_FP32_DF64. */
 cdbm_status cdbm_state_ptr(cdbm_ctx *ctx, void **f);
 
 /* Simulated time (host scalar). */
@@ -220,8 +225,8 @@ void cdbm_destroy(cdbm_ctx *ctx);
  * [16][total_cells].  One persistent kernel advances every tube through all
  * requested steps; a block owns a fixed set of whole tubes, so blocks never wait on
  * one another (block barriers only, between Runge-Kutta stages).  The two-stage TVD
- * scheme is used.  Precision: CDBM_FP64 or CDBM_FP32_BULK (per-tube reference F =
- * f_eq of the tube's mean rho and T).
+ * scheme is used.  Precision: CDBM_FP64, CDBM_FP32_BULK or CDBM_FP32_DF64 (single
+ * precision with a per-tube reference F = f_eq of the tube's mean rho and T).
  * ---------------------------------------------------------------------------- */
 typedef struct cdbm_batch cdbm_batch;
 

@@ -295,7 +295,7 @@ void set_reference(cdbm_ctx *c, double rho0, double T0)
     const double K = c->mc.K, P0 = rho0 * T0;
     for (int g = 0; g < 4; ++g) {
         const double *S = c->eq_unit.S + 4 * g;
-        c->Fg[g] = (c->precision == CDBM_FP32_BULK && std::isfinite(rho0) && std::isfinite(T0))
+        c->Fg[g] = (single_storage(c->precision) && std::isfinite(rho0) && std::isfinite(T0))
                        ? S[0] * rho0 + S[1] * K * P0 + S[3] * 2.0 * (K + 2.0) * P0 * T0
                        : 0.0;
         c->fields.Fg[g] = c->Fg[g];
@@ -334,6 +334,7 @@ void build_stages(cdbm_ctx *c)
         a.ny = c->grid.ny;
         a.bc_x = c->grid.bc_x;
         a.bc_y = c->grid.bc_y;
+        fill_df_consts(a);
         c->launch[s] = stage_launch_config(a, r.with_base, c->sm_count, c->precision);
     }
 }
@@ -414,7 +415,7 @@ cdbm_status cdbm_create(const cdbm_grid *grid, const cdbm_vset *vset, double I, 
     if (!(std::isfinite(I) && I >= 0.0)) return create_err(CDBM_EINVAL, "I must be finite and >= 0");
     if ((grid->bc_x != 0 && grid->bc_x != 1) || (grid->bc_y != 0 && grid->bc_y != 1))
         return create_err(CDBM_EINVAL, "unknown boundary kind");
-    if (precision != CDBM_FP64 && precision != CDBM_FP32_BULK)
+    if (precision != CDBM_FP64 && precision != CDBM_FP32_BULK && precision != CDBM_FP32_DF64)
         return create_err(CDBM_EINVAL, "unsupported precision %d", precision);
     for (int g = 0; g < 4; ++g)
         if (!std::isfinite(vset->v[g]) || !std::isfinite(vset->eta[g]) || vset->v[g] <= 0.0 ||
@@ -535,7 +536,7 @@ cdbm_status cdbm_init(cdbm_ctx *c, const double *rho, const double *ux, const do
             dev[k] = dst;
         }
     }
-    if (c->precision == CDBM_FP32_BULK) {
+    if (single_storage(c->precision)) {
         // reference state for the deviation storage: the means of rho and T
         double sum[2] = {0.0, 0.0};
         if (cuda_check(c, launch_field_means(dev[0], dev[3], c->plane, c->partials, c->sum_blocks, c->sums,

@@ -20,7 +20,7 @@
 #include <numeric>
 #include <vector>
 
-#include "cdbm_device.cuh"
+#include "cdbm_df64.cuh"
 #include "cdbm_internal.h"
 
 using namespace cdbm;
@@ -38,12 +38,15 @@ struct TubeInfo {
     double sF[2][4];                  // per stage: gamma h F_g (FP32-bulk reference)
     double Fg[4];                     // reference equilibrium per group
     double rhoF, EF;                  // its conserved moments
+    DFShift dfs[2];                   // per stage: the same in df64 (CDBM_FP32_DF64)
 };
 
 struct ClassConsts {
     EqBlocks eq[2];                   // per stage, scaled by gamma h
     EqBlocks unit;                    // unscaled (initialisation, macros)
     ModelConsts m;
+    DFBlocks dfeq[2];                 // eq[] and m in df64 (CDBM_FP32_DF64)
+    DFModel dfm;
 };
 
 struct BatchArgs {
@@ -59,33 +62,44 @@ __device__ __forceinline__ TS pick(double d, float f)
     if constexpr (kSingle<TS>) return f; else return d;
 }
 
-// One Runge-Kutta stage over the nx cells of one tube by the calling block.  g, base
-// and out point at the tube's first cell; planes are P apart.  The arithmetic per
-// cell is the flat (Ny = 1) stage of the single-grid kernels.  Plain loads: the
-// buffers are written inside this kernel, so the read-only path may not be used.
-template <typename TS, bool kBase>
-__device__ __forceinline__ void tube_stage(const TS *g, const TS *base, TS *out, long long P, int nx,
-                                           const EqBlocks &eq, const ModelConsts &m, TS a_self,
-                                           TS a_base, const double *lx, const float *lx_f,
-                                           const double *sF, double rhoF, double EF, unsigned *flag)
+// One Runge-Kutta stage (kStage 0 or 1) over the nx cells of one tube by the calling
+// block.  g, base and out point at the tube's first cell; planes are P apart.  The
+// arithmetic per cell is the flat (Ny = 1) stage of the single-grid kernels, with the
+// equilibrium in double or, with kDF, in df64.  Plain loads: the buffers are written
+// inside this kernel, so the read-only path may not be used.
+template <typename TS, int kStage, bool kDF>
+__device__ __forceinline__ void tube_stage(const TS *g, const TS *base, TS *out, long long P,
+                                           const TubeInfo &t, const ClassConsts &C, TS a_self, TS a_base,
+                                           unsigned *flag)
 {
+    constexpr bool kBase = kStage == 1;
+    const int nx = t.nx;
+    const double *lx = t.lx[kStage];
+    const float *lx_f = t.lx_f[kStage];
     for (int x = threadIdx.x; x < nx; x += blockDim.x) {
         const int xm2 = x >= 2 ? x - 2 : 0, xm1 = x >= 1 ? x - 1 : 0;
         const int xp1 = x + 1 < nx ? x + 1 : nx - 1, xp2 = x + 2 < nx ? x + 2 : nx - 1;
         TS fs[kNV];
-        double f[kNV];
 #pragma unroll
-        for (int i = 0; i < kNV; ++i) {
-            fs[i] = g[i * P + x];
-            f[i] = (double)fs[i];
+        for (int i = 0; i < kNV; ++i) fs[i] = g[i * P + x];
+        TS heq[kNV];
+        if constexpr (kDF) {
+            static_assert(kSingle<TS>, "df64 equilibrium is for the single-precision state");
+            df_equilibrium(C.dfeq[kStage], C.dfm, t.dfs[kStage], fs, heq, flag);
+        } else {
+            double f[kNV];
+#pragma unroll
+            for (int i = 0; i < kNV; ++i) f[i] = (double)fs[i];
+            const Prim s = primitives<kSingle<TS>>(f, C.m, t.rhoF, t.EF, flag);
+            double h[kNV];
+            equilibrium<kSingle<TS>>(C.eq[kStage], C.m, s.q.rho, s.q.E, s.q.jx, s.q.jy, s.ux, s.uy, s.ru2,
+                                     s.jyuy, s.p, s.T, h, t.sF[kStage]);
+#pragma unroll
+            for (int i = 0; i < kNV; ++i) heq[i] = (TS)h[i];
         }
-        const Prim s = primitives<kSingle<TS>>(f, m, rhoF, EF, flag);
-        double heq[kNV];
-        equilibrium<kSingle<TS>>(eq, m, s.q.rho, s.q.E, s.q.jx, s.q.jy, s.ux, s.uy, s.ru2, s.jyuy, s.p,
-                                 s.T, heq, sF);
 #pragma unroll
         for (int i = 0; i < kNV; ++i) {
-            TS o = fma_t(a_self, fs[i], (TS)heq[i]);
+            TS o = fma_t(a_self, fs[i], heq[i]);
             if (kBase) o = fma_t(a_base, base[i * P + x], o);
             if (dirx(i) != 0) {
                 const TS *gp = g + i * P;
@@ -99,7 +113,7 @@ __device__ __forceinline__ void tube_stage(const TS *g, const TS *base, TS *out,
     }
 }
 
-template <typename TS, int kThreads>
+template <typename TS, int kThreads, bool kDF>
 __global__ void __launch_bounds__(kThreads, (384 / kThreads > 0 ? 384 / kThreads : 1)) batch_kernel(TS *f, TS *f1, const TubeInfo *tubes,
                                                          const int *work, const int *work_off, int nsteps,
                                                          const BatchArgs a, unsigned *flag)
@@ -112,11 +126,9 @@ __global__ void __launch_bounds__(kThreads, (384 / kThreads > 0 ? 384 / kThreads
         TS *ft = f + t.offset;
         TS *f1t = f1 + t.offset;
         for (int s = 0; s < nsteps; ++s) {
-            tube_stage<TS, false>(ft, nullptr, f1t, a.P, t.nx, C.eq[0], C.m, as0, ab0, t.lx[0], t.lx_f[0],
-                                  t.sF[0], t.rhoF, t.EF, flag);
+            tube_stage<TS, 0, kDF>(ft, nullptr, f1t, a.P, t, C, as0, ab0, flag);
             __syncthreads();
-            tube_stage<TS, true>(f1t, ft, ft, a.P, t.nx, C.eq[1], C.m, as1, ab1, t.lx[1], t.lx_f[1],
-                                 t.sF[1], t.rhoF, t.EF, flag);
+            tube_stage<TS, 1, kDF>(f1t, ft, ft, a.P, t, C, as1, ab1, flag);
             __syncthreads();
         }
     }
@@ -187,14 +199,21 @@ __global__ void __launch_bounds__(128) batch_macros_kernel(const BatchArgs a, co
     }
 }
 
-template <typename TS>
-void *batch_func(int threads)
+template <typename TS, bool kDF>
+void *batch_func_t(int threads)
 {
     switch (threads) {
-    case 64: return (void *)batch_kernel<TS, 64>;
-    case 256: return (void *)batch_kernel<TS, 256>;
-    default: return (void *)batch_kernel<TS, 128>;
+    case 64: return (void *)batch_kernel<TS, 64, kDF>;
+    case 256: return (void *)batch_kernel<TS, 256, kDF>;
+    default: return (void *)batch_kernel<TS, 128, kDF>;
     }
+}
+
+void *batch_func(int precision, int threads)
+{
+    if (precision == CDBM_FP32_DF64) return batch_func_t<float, true>(threads);
+    if (precision == CDBM_FP32_BULK) return batch_func_t<float, false>(threads);
+    return batch_func_t<double, false>(threads);
 }
 
 }  // namespace
@@ -347,7 +366,7 @@ cdbm_status launch_run(cdbm_batch *b, int nsteps)
     const TubeInfo *tubes = b->d_tubes;
     const int *work = b->d_work, *off = b->d_work_off;
     void *args[] = {&f, &f1, (void *)&tubes, (void *)&work, (void *)&off, &nsteps, (void *)&b->args, &b->flag};
-    void *fn = b->precision == CDBM_FP32_BULK ? batch_func<float>(b->threads) : batch_func<double>(b->threads);
+    void *fn = batch_func(b->precision, b->threads);
     return bcuda(b, cudaLaunchKernel(fn, dim3(b->blocks), dim3(b->threads), args, 0, b->stream), "batch launch");
 }
 
@@ -362,7 +381,7 @@ cdbm_status run_graph(cdbm_batch *b, int nsteps)
         void *args[] = {&f, &f1, (void *)&tubes, (void *)&work, (void *)&off, &nsteps, (void *)&b->args, &b->flag};
         cudaKernelNodeParams p;
         memset(&p, 0, sizeof(p));
-        p.func = b->precision == CDBM_FP32_BULK ? batch_func<float>(b->threads) : batch_func<double>(b->threads);
+        p.func = batch_func(b->precision, b->threads);
         p.gridDim = dim3(b->blocks);
         p.blockDim = dim3(b->threads);
         p.kernelParams = args;
@@ -397,7 +416,7 @@ cdbm_status cdbm_batch_create(int ntubes, const int *nx, const double *dx, const
     if (!(std::isfinite(dt) && dt > 0 && std::isfinite(tau) && tau > 0))
         return bcreate_err(CDBM_EINVAL, "dt and tau must be finite and > 0");
     if (dt / tau > 2.0) return bcreate_err(CDBM_EINVAL, "dt/tau = %g exceeds 2", dt / tau);
-    if (precision != CDBM_FP64 && precision != CDBM_FP32_BULK)
+    if (precision != CDBM_FP64 && precision != CDBM_FP32_BULK && precision != CDBM_FP32_DF64)
         return bcreate_err(CDBM_EINVAL, "unsupported precision %d", precision);
     double vmax = 0.0;
     for (int g = 0; g < 4; ++g) {
@@ -453,7 +472,11 @@ cdbm_status cdbm_batch_create(int ntubes, const int *nx, const double *dx, const
                 delete b;
                 return bcreate_err(CDBM_ESINGULAR, "moment matrix block '%s' singular (cond %g)", which, cond);
             }
-            for (int s = 0; s < 2; ++s) C.eq[s] = scaled(C.unit, gamma[s] * h);
+            for (int s = 0; s < 2; ++s) {
+                C.eq[s] = scaled(C.unit, gamma[s] * h);
+                C.dfeq[s] = df_blocks(C.eq[s]);
+            }
+            C.dfm = df_model(C.m);
         }
         TubeInfo &ti = b->info[t];
         memset(&ti, 0, sizeof(ti));
@@ -543,21 +566,23 @@ cdbm_status cdbm_batch_init(cdbm_batch *b, const double *rho, const double *ux, 
         ti.rhoF = ti.EF = 0.0;
         for (int g = 0; g < 4; ++g) {
             const double *S = C.unit.S + 4 * g;
-            ti.Fg[g] = b->precision == CDBM_FP32_BULK
+            ti.Fg[g] = single_storage(b->precision)
                            ? S[0] * r0 + S[1] * K * P0 + S[3] * 2.0 * (K + 2.0) * P0 * T0
                            : 0.0;
             ti.rhoF += 4.0 * ti.Fg[g];
             ti.EF += 4.0 * ti.Fg[g] * C.m.w[g];
         }
         const double h = b->dt / b->tau, gamma[2] = {1.0, 0.5};
-        for (int s = 0; s < 2; ++s)
+        for (int s = 0; s < 2; ++s) {
             for (int g = 0; g < 4; ++g) ti.sF[s][g] = gamma[s] * h * ti.Fg[g];
+            ti.dfs[s] = df_shift(ti.sF[s], ti.rhoF, ti.EF);
+        }
     }
     const unsigned nb = cells_grid(b->P);
     if (bcuda(b, cudaMemcpyAsync(b->d_tubes, b->info.data(), sizeof(TubeInfo) * b->ntubes, cudaMemcpyHostToDevice,
                                  b->stream), "tube upload"))
         return b->err;
-    if (b->precision == CDBM_FP32_BULK)
+    if (single_storage(b->precision))
         batch_init_kernel<float><<<nb, 128, 0, b->stream>>>(b->args, b->d_tubes, b->d_offs, b->ntubes, dev[0], dev[1],
                                                             dev[2], dev[3], (float *)b->f, b->flag);
     else
@@ -657,7 +682,7 @@ cdbm_status cdbm_batch_macros(cdbm_batch *b, double *rho, double *ux, double *uy
         dev[k] = host[k] ? stage + k * n : dst[k];
     }
     const unsigned nb = cells_grid(b->P);
-    if (b->precision == CDBM_FP32_BULK)
+    if (single_storage(b->precision))
         batch_macros_kernel<float><<<nb, 128, 0, b->stream>>>(b->args, b->d_tubes, b->d_offs, b->ntubes,
                                                               (const float *)b->f, dev[0], dev[1], dev[2], dev[3]);
     else

@@ -46,6 +46,28 @@ struct ModelConsts {
     double Kp2, Kp4, Kp6, twoKp2;   // K + 2, K + 4, K + 6, 2 (K + 2)
 };
 
+// Double-float copies of the stage constants for CDBM_FP32_DF64 (each value as the
+// unevaluated sum of two floats; see cdbm_df64.cuh).
+struct DFPair {
+    float hi, lo;
+};
+struct DFBlocks {                 // EqBlocks (scaled per stage)
+    DFPair S[16], V[16], B1[4], B2[4];
+};
+struct DFModel {                  // the ModelConsts the equilibrium uses
+    DFPair c[4], w[4];
+    DFPair invK, Kp4, Kp6, twoKp2;
+};
+struct DFShift {                  // reference state of the deviation storage
+    DFPair sF[4];                 // gamma h F_g
+    DFPair rhoF, EF;
+};
+struct DFConsts {
+    DFBlocks b;
+    DFModel m;
+    DFShift r;
+};
+
 // One Runge-Kutta stage: out = a_base * base + a_self * g + eq(g) - sum_r l_r D_r(g),
 // i.e. alpha f^n + beta g + gamma dt L(g) with a_self = beta - gamma h, the
 // equilibrium blocks scaled by gamma h and l = gamma dt c_g / dr.
@@ -65,6 +87,7 @@ struct StageArgs {
     // cancel because alpha + beta = 1 in every stage.
     double sF[4];
     double rhoF, EF;
+    DFConsts d;                   // df64 copies (CDBM_FP32_DF64)
     int nx, ny;
     int bc_x, bc_y;
 };
@@ -133,7 +156,15 @@ cudaError_t launch_macros_vjp(const FieldArgs &a, const double *f, const double 
                               const double *uy_bar, const double *T_bar, double *fbar, cudaStream_t s);
 cudaError_t launch_sum(const double *v, int n, double *out, cudaStream_t s);
 
+// Single-precision storage (FP32 bulk, with the equilibrium in double or in df64).
+inline bool single_storage(int prec) { return prec == CDBM_FP32_BULK || prec == CDBM_FP32_DF64; }
 // Bytes of one distribution value in storage precision `prec`.
-inline size_t storage_bytes(int prec) { return prec == CDBM_FP32_BULK ? 4 : 8; }
+inline size_t storage_bytes(int prec) { return single_storage(prec) ? 4 : 8; }
+// Double-float copies of double constants (host side, cdbm_kernels.cu).
+DFBlocks df_blocks(const EqBlocks &e);
+DFModel df_model(const ModelConsts &m);
+DFShift df_shift(const double sF[4], double rhoF, double EF);
+// Fills a.d from the double constants of a.
+void fill_df_consts(StageArgs &a);
 
 }  // namespace cdbm

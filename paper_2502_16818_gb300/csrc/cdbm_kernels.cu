@@ -1,14 +1,15 @@
 // CDBM kernels: initial equilibrium, the fused Runge-Kutta stage, macroscopic
 // fields, nonequilibrium moments and conserved sums.  The distribution buffers
-// are stored in double (CDBM_FP64) or single (CDBM_FP32_BULK) precision, selected
-// by the template parameter TS; conserved sums and the equilibrium are always
-// computed in double.
+// are stored in double (CDBM_FP64) or single (CDBM_FP32_BULK, CDBM_FP32_DF64)
+// precision, selected by the template parameter TS; the conserved sums and the
+// equilibrium of a stage are computed in double, or in double-float arithmetic
+// on the FP32 pipe for CDBM_FP32_DF64 (template flag kDF).
 //
 // Layout: f[16][ny][nx] (velocity plane outermost, x fastest).  One thread owns
 // one cell; a block covers a run of cells along x of one row, so centre loads
 // and stores of a warp are coalesced rows and the stencil neighbours
 // (x +- 1, 2 and the rows y +- 1, 2) are served from L1/L2.
-#include "cdbm_device.cuh"
+#include "cdbm_df64.cuh"
 
 namespace cdbm {
 
@@ -44,6 +45,29 @@ __device__ __forceinline__ TS ly_of(const StageArgs &a, int g)
 // Stored value of velocity i -> f_i in double (adds the reference F to an FP32 deviation).
 __device__ __forceinline__ double widen(const FieldArgs &, double v, int) { return v; }
 __device__ __forceinline__ double widen(const FieldArgs &a, float v, int i) { return a.Fg[i >> 2] + (double)v; }
+
+// gamma h f_eq of one cell in the storage precision (minus gamma h F for the
+// single-precision deviation state): moments, primitives and equilibrium in double,
+// or all of it in df64 when kDF.
+template <typename TS, bool kDF>
+__device__ __forceinline__ void stage_equilibrium(const StageArgs &a, const TS fs[kNV], TS heq[kNV],
+                                                  unsigned *flag)
+{
+    if constexpr (kDF) {
+        static_assert(kSingle<TS>, "df64 equilibrium is for the single-precision state");
+        df_equilibrium(a.d.b, a.d.m, a.d.r, fs, heq, flag);
+    } else {
+        double f[kNV];
+#pragma unroll
+        for (int i = 0; i < kNV; ++i) f[i] = (double)fs[i];
+        const Prim s = primitives<kSingle<TS>>(f, a.m, a.rhoF, a.EF, flag);
+        double h[kNV];
+        equilibrium<kSingle<TS>>(a.eq, a.m, s.q.rho, s.q.E, s.q.jx, s.q.jy, s.ux, s.uy, s.ru2, s.jyuy,
+                                 s.p, s.T, h, a.sF);
+#pragma unroll
+        for (int i = 0; i < kNV; ++i) heq[i] = (TS)h[i];
+    }
+}
 
 // ---------------------------------------------------------------- init (K0)
 
@@ -81,7 +105,7 @@ __global__ void __launch_bounds__(128) init_kernel(const FieldArgs a, const doub
 
 // out = a_base base + a_self g + gamma h f_eq(g) - sum_r l_r D_r(g) for one cell:
 // macros -> equilibrium -> BGK -> NND transport of all 16 velocities -> update.
-template <typename TS, bool kBase, bool kFlatY>
+template <typename TS, bool kBase, bool kFlatY, bool kDF>
 __global__ void __launch_bounds__(kStageThreads, CDBM_STAGE_MIN_BLOCKS)
     stage_kernel(const TS *__restrict__ g, const TS *base, TS *out, const StageArgs a, unsigned *flag)
 {
@@ -102,22 +126,16 @@ __global__ void __launch_bounds__(kStageThreads, CDBM_STAGE_MIN_BLOCKS)
             rp2 = (size_t)neighbour(y + 2, ny, a.bc_y) * nx + x;
         }
         TS fs[kNV];
-        double f[kNV];
 #pragma unroll
-        for (int i = 0; i < kNV; ++i) {
-            fs[i] = __ldg(g + i * P + c);
-            f[i] = (double)fs[i];
-        }
-        const Prim s = primitives<kSingle<TS>>(f, a.m, a.rhoF, a.EF, flag);
-        double heq[kNV];
-        equilibrium<kSingle<TS>>(a.eq, a.m, s.q.rho, s.q.E, s.q.jx, s.q.jy, s.ux, s.uy, s.ru2, s.jyuy,
-                                 s.p, s.T, heq, a.sF);
+        for (int i = 0; i < kNV; ++i) fs[i] = __ldg(g + i * P + c);
+        TS heq[kNV];
+        stage_equilibrium<TS, kDF>(a, fs, heq, flag);
 
 #pragma unroll
         for (int i = 0; i < kNV; ++i) {
             const int grp = i >> 2;
             const TS *gp = g + i * P;
-            TS o = fma_t(a_self_of<TS>(a), fs[i], (TS)heq[i]);
+            TS o = fma_t(a_self_of<TS>(a), fs[i], heq[i]);
             if (kBase) o = fma_t(a_base_of<TS>(a), base[i * P + c], o);
             if (dirx(i) != 0) {
                 const TS u2 = __ldg(gp + row + (dirx(i) > 0 ? xm2 : xp2));
@@ -150,7 +168,7 @@ __host__ __device__ constexpr int yvel(int k)       // k-th velocity with diry !
     return k < 2 ? 1 + 2 * k : (k < 6 ? k + 2 : (k < 8 ? 9 + 2 * (k - 6) : k + 4));
 }
 
-template <typename TS, bool kBase>
+template <typename TS, bool kBase, bool kDF>
 __global__ void __launch_bounds__(kStageThreads, CDBM_STAGE_MIN_BLOCKS)
     stage_march_kernel(const TS *__restrict__ g, const TS *base, TS *out, const StageArgs a, unsigned *flag)
 {
@@ -199,21 +217,15 @@ __global__ void __launch_bounds__(kStageThreads, CDBM_STAGE_MIN_BLOCKS)
         const size_t rp1 = (size_t)neighbour(y + 1, ny, a.bc_y) * nx + x;
         const size_t rp2 = (size_t)neighbour(y + 2, ny, a.bc_y) * nx + x;
         TS fs[kNV];
-        double f[kNV];
 #pragma unroll
-        for (int i = 0; i < kNV; ++i) {
-            fs[i] = __ldg(g + i * P + c);
-            f[i] = (double)fs[i];
-        }
-        const Prim s = primitives<kSingle<TS>>(f, a.m, a.rhoF, a.EF, flag);
-        double heq[kNV];
-        equilibrium<kSingle<TS>>(a.eq, a.m, s.q.rho, s.q.E, s.q.jx, s.q.jy, s.ux, s.uy, s.ru2, s.jyuy,
-                                 s.p, s.T, heq, a.sF);
+        for (int i = 0; i < kNV; ++i) fs[i] = __ldg(g + i * P + c);
+        TS heq[kNV];
+        stage_equilibrium<TS, kDF>(a, fs, heq, flag);
 
         TS o[kNV];
 #pragma unroll
         for (int i = 0; i < kNV; ++i) {
-            o[i] = fma_t(a_self_of<TS>(a), fs[i], (TS)heq[i]);
+            o[i] = fma_t(a_self_of<TS>(a), fs[i], heq[i]);
             if (kBase) o[i] = fma_t(a_base_of<TS>(a), base[i * P + c], o[i]);
             if (dirx(i) != 0) {
                 const TS *gp = g + i * P + row;
@@ -420,14 +432,14 @@ unsigned grid_for(size_t cells, int threads)
     return (unsigned)(b < 1 ? 1 : (b > 1048576 ? 1048576 : b));
 }
 
-template <typename TS>
+template <typename TS, bool kDF>
 void *stage_func(bool march, bool with_base, bool flat)
 {
     if (march)
-        return with_base ? (void *)stage_march_kernel<TS, true> : (void *)stage_march_kernel<TS, false>;
+        return with_base ? (void *)stage_march_kernel<TS, true, kDF> : (void *)stage_march_kernel<TS, false, kDF>;
     if (with_base)
-        return flat ? (void *)stage_kernel<TS, true, true> : (void *)stage_kernel<TS, true, false>;
-    return flat ? (void *)stage_kernel<TS, false, true> : (void *)stage_kernel<TS, false, false>;
+        return flat ? (void *)stage_kernel<TS, true, true, kDF> : (void *)stage_kernel<TS, true, false, kDF>;
+    return flat ? (void *)stage_kernel<TS, false, true, kDF> : (void *)stage_kernel<TS, false, false, kDF>;
 }
 
 }  // namespace
@@ -436,7 +448,7 @@ cudaError_t launch_init(const FieldArgs &a, const double *rho, const double *ux,
                         const double *T, void *f, int prec, unsigned *flag, cudaStream_t s)
 {
     const unsigned nb = grid_for((size_t)a.nx * a.ny, 128);
-    if (prec == CDBM_FP32_BULK)
+    if (single_storage(prec))
         init_kernel<float><<<nb, 128, 0, s>>>(a, rho, ux, uy, T, (float *)f, flag);
     else
         init_kernel<double><<<nb, 128, 0, s>>>(a, rho, ux, uy, T, (double *)f, flag);
@@ -447,7 +459,7 @@ cudaError_t launch_macros(const FieldArgs &a, const void *f, int prec, double *r
                           double *uy, double *T, cudaStream_t s)
 {
     const unsigned nb = grid_for((size_t)a.nx * a.ny, 128);
-    if (prec == CDBM_FP32_BULK)
+    if (single_storage(prec))
         macros_kernel<float><<<nb, 128, 0, s>>>(a, (const float *)f, rho, ux, uy, T);
     else
         macros_kernel<double><<<nb, 128, 0, s>>>(a, (const double *)f, rho, ux, uy, T);
@@ -457,7 +469,7 @@ cudaError_t launch_macros(const FieldArgs &a, const void *f, int prec, double *r
 cudaError_t launch_tne(const FieldArgs &a, const void *f, int prec, double *out, cudaStream_t s)
 {
     const unsigned nb = grid_for((size_t)a.nx * a.ny, 128);
-    if (prec == CDBM_FP32_BULK)
+    if (single_storage(prec))
         tne_kernel<float><<<nb, 128, 0, s>>>(a, (const float *)f, out);
     else
         tne_kernel<double><<<nb, 128, 0, s>>>(a, (const double *)f, out);
@@ -467,7 +479,7 @@ cudaError_t launch_tne(const FieldArgs &a, const void *f, int prec, double *out,
 cudaError_t launch_sums(const FieldArgs &a, const void *f, int prec, double *partials, int nblocks,
                         double *out4, cudaStream_t s)
 {
-    if (prec == CDBM_FP32_BULK)
+    if (single_storage(prec))
         sums_partial_kernel<float><<<nblocks, kSumThreads, 0, s>>>(a, (const float *)f, partials);
     else
         sums_partial_kernel<double><<<nblocks, kSumThreads, 0, s>>>(a, (const double *)f, partials);
@@ -480,7 +492,7 @@ cudaError_t launch_convert(const FieldArgs &a, const void *src, int src_prec, vo
 {
     const size_t plane = (size_t)a.nx * a.ny;
     const unsigned nb = grid_for(kNV * plane, 256);
-    const bool si = src_prec == CDBM_FP32_BULK, so = dst_prec == CDBM_FP32_BULK;
+    const bool si = single_storage(src_prec), so = single_storage(dst_prec);
     if (si && !so)
         widen_kernel<<<nb, 256, 0, s>>>(a, (const float *)src, (double *)dst, plane);
     else if (!si && so)
@@ -510,8 +522,9 @@ StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count
     int R = 8;
     while (R < 32 && (size_t)xblocks * ((a.ny + 2 * R - 1) / (2 * R)) >= 8 * wave) R *= 2;
     const bool march = !flat && a.ny >= 16 && (size_t)xblocks * ((a.ny + 7) / 8) >= 2 * wave;
-    L.func = prec == CDBM_FP32_BULK ? stage_func<float>(march, with_base, flat)
-                                    : stage_func<double>(march, with_base, flat);
+    L.func = prec == CDBM_FP32_DF64   ? stage_func<float, true>(march, with_base, flat)
+             : prec == CDBM_FP32_BULK ? stage_func<float, false>(march, with_base, flat)
+                                      : stage_func<double, false>(march, with_base, flat);
     if (march) {
         L.block = dim3(kStageThreads, 1, 1);
         const unsigned yblocks = (unsigned)((a.ny + R - 1) / R);
@@ -524,6 +537,50 @@ StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count
     L.block = dim3(threads, 1, 1);
     L.grid = dim3((a.nx + threads - 1) / threads, a.ny < 65535 ? a.ny : 65535, 1);
     return L;
+}
+
+DFBlocks df_blocks(const EqBlocks &e)
+{
+    DFBlocks d;
+    for (int k = 0; k < 16; ++k) {
+        d.S[k] = df_from(e.S[k]);
+        d.V[k] = df_from(e.V[k]);
+    }
+    for (int k = 0; k < 4; ++k) {
+        d.B1[k] = df_from(e.B1[k]);
+        d.B2[k] = df_from(e.B2[k]);
+    }
+    return d;
+}
+
+DFModel df_model(const ModelConsts &m)
+{
+    DFModel d;
+    for (int k = 0; k < 4; ++k) {
+        d.c[k] = df_from(m.c[k]);
+        d.w[k] = df_from(m.w[k]);
+    }
+    d.invK = df_from(m.invK);
+    d.Kp4 = df_from(m.Kp4);
+    d.Kp6 = df_from(m.Kp6);
+    d.twoKp2 = df_from(m.twoKp2);
+    return d;
+}
+
+DFShift df_shift(const double sF[4], double rhoF, double EF)
+{
+    DFShift d;
+    for (int k = 0; k < 4; ++k) d.sF[k] = df_from(sF[k]);
+    d.rhoF = df_from(rhoF);
+    d.EF = df_from(EF);
+    return d;
+}
+
+void fill_df_consts(StageArgs &a)
+{
+    a.d.b = df_blocks(a.eq);
+    a.d.m = df_model(a.m);
+    a.d.r = df_shift(a.sF, a.rhoF, a.EF);
 }
 
 cudaError_t launch_stage(const StageLaunch &L, const void *g, const void *base, void *out,

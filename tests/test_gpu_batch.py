@@ -2,7 +2,8 @@
 
 Each tube of a batch is an independent Ny = 1 run; the oracle runs every checked
 tube on its own.  Acceptance: FP64 batch <= 1e-10 relative max-norm on rho, u, T
-(as the single-grid path); FP32-bulk batch <= 1e-5 relative L2 density error.
+(as the single-grid path); single-precision batches (FP32_BULK, FP32_DF64) <= 1e-5
+relative L2 density error.
 The result of a batch does not depend on its tile (threads per block, partition):
 each cell's arithmetic is the same, so states agree bit for bit.
 """
@@ -67,10 +68,10 @@ def test_batch_fp64_matches_oracle_per_tube():
         assert rel(got[3], ref[3][0]) <= 1e-10, t
 
 
-def test_batch_fp32_bulk_matches_oracle_per_tube():
-    from paper_2502_16818_gb300 import CDBM_FP32_BULK
+@pytest.mark.parametrize("precision", [1, 2], ids=["fp32_bulk", "fp32_df64"])
+def test_batch_single_precision_matches_oracle_per_tube(precision):
     tubes = tubes_small(seed=4)
-    b, out = run_batch(tubes, 200, precision=CDBM_FP32_BULK)
+    b, out = run_batch(tubes, 200, precision=precision)
     for t, w in enumerate(tubes):
         got = b.tube(out, t)
         ref = oracle_tube(w, 200)
@@ -78,7 +79,7 @@ def test_batch_fp32_bulk_matches_oracle_per_tube():
         assert l2 <= 1e-5, (t, l2)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_batch_result_independent_of_tile(precision):
     tubes = tubes_small(n=40, seed=5, steps=30)
     outs = [run_batch(tubes, 30, precision, tile=tile)[1] for tile in ((64, 1), (128, 3), (256, 4))]
@@ -102,7 +103,7 @@ def test_batch_matches_single_grid_path():
             assert np.array_equal(a, c)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_full_ensemble_sampled_tubes(precision):
     """The configured ensemble: 1024 tubes, Nx ~ U{200..4000} (seed 0), 1000 steps,
     autotuned tile; four tubes (shortest, longest, two others) checked against the
