@@ -146,7 +146,7 @@ def cpu_sample(w, side):
     return m, sub
 
 
-def cpu_baseline(w, side=1024, steps=2):
+def cpu_baseline(w, side=2048, steps=8):
     """The oracle (as it stands) on the host cores: `steps` steps on a side^2 sample."""
     import oracle
     m, sub = cpu_sample(w, side)
@@ -155,8 +155,8 @@ def cpu_baseline(w, side=1024, steps=2):
     oracle.step(m, f, steps)
     dt = time.perf_counter() - t0
     return {"value": side * side * steps / dt, "unit": UNIT, "cores": m.threads, "kind": "oracle",
-            "sample": "%dx%d block of the 4096^2 Taylor-Green initial state, %d RK2 steps, "
-                      "zero-gradient edges, %.1f s wall" % (side, side, steps, dt)}
+            "sample": "%dx%d block of the %d^2 Taylor-Green initial state, %d RK2 steps, "
+                      "zero-gradient edges, %.1f s wall" % (side, side, w.nx, steps, dt)}
 
 
 def run_reference(a, rank, world):
@@ -292,8 +292,9 @@ def run_cdbm(a, rank, world, local_rank):
             out["ensemble"] = ensemble(a, torch)
         if a.adj_steps > 0:
             out["adjoint"] = adjoint(a, torch)
+        out["configs"] = configs(a, torch)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(w)
+        out["cpu_baseline"] = cpu_baseline(w, side=min(2048, w.nx))
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -370,6 +371,38 @@ def ensemble(a, torch):
                                  "steps": loop_steps, "gpu_launches": 2 * loop_steps * len(tubes)}
     res["batched_fp32_vs_fp64_plain_loop"] = res["fp32_bulk_batched"]["value"] / res["fp64_per_tube_loop"]["value"]
     res["batched_df64_vs_fp64_plain_loop"] = res["fp32_df64_batched"]["value"] / res["fp64_per_tube_loop"]["value"]
+    return res
+
+
+def configs(a, torch):
+    """Wall time of the paper-scale configurations on the GPU (CUDA events around the
+    whole run, state resident): Sod (500 cells, 10^4 steps), Lax (2000 cells, 10^4
+    steps) and the 512^2 sound wave for I = 0, 1, 3 (2000 steps), in FP64 and with
+    the single-precision state and df64 equilibrium."""
+    from paper_2502_16818_gb300 import CDBM_FP32_DF64, CDBM_FP64, Solver, workloads as W
+    runs = [("sod_500_I0", W.sod(nx=500, I=0.0), 10000), ("lax_2000_I0", W.lax(nx=2000, I=0.0), 10000)]
+    runs += [("sound_512_I%d" % I, W.sound(n=512, I=float(I)), 2000) for I in (0, 1, 3)]
+    res = {}
+    for name, w, steps in runs:
+        row = {"cells": w.nx * w.ny, "steps": steps}
+        for label, prec in (("fp64", CDBM_FP64), ("fp32_df64", CDBM_FP32_DF64)):
+            st = torch.cuda.Stream()
+            with torch.cuda.stream(st):
+                s = Solver.from_workload(w, stream=st, precision=prec)
+                s.init(*(torch.from_numpy(x).to("cuda") for x in (w.rho, w.ux, w.uy, w.T)))
+                s.step(64)
+                s.init(*(torch.from_numpy(x).to("cuda") for x in (w.rho, w.ux, w.uy, w.T)))
+            s.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            s.step(steps)
+            e1.record(st)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            s.sync()
+            s.close()
+            row[label] = {"run_ms": ms, "value": row["cells"] * steps / (ms * 1e-3), "unit": UNIT}
+        res[name] = row
     return res
 
 

@@ -200,6 +200,20 @@ cdbm_status cdbm_adjoint_forward(cdbm_ctx *ctx, int nsteps, int every);
 cdbm_status cdbm_adjoint_backward(cdbm_ctx *ctx, const double *fbar, double *grad_rho, double *grad_ux,
                                   double *grad_uy, double *grad_T, double *grad_tau);
 
+/* Tie band b of the limiter derivative used by cdbm_adjoint_backward, 0 <= b <= 1
+ * (default 0).  With b = 0 the limiter enters through the derivative of the branch
+ * the forward pass took, i.e. the adjoint is the exact derivative of the discrete
+ * step.  With b > 0, two same-signed minmod arguments whose magnitudes differ by
+ * less than b max(|X|, |Y|) share the derivative on a linear ramp,
+ * w_X = (1 + t)/2, w_Y = 1 - w_X, t = clamp((|Y| - |X|) / (b max(|X|, |Y|)), -1, 1);
+ * outside the band the branch derivative is used unchanged.  This is a
+ * regularisation, not part of the paper's scheme (Eqs. 12-20): where the limiter
+ * picks between nearly equal slopes the exact linearisation can be anti-diffusive,
+ * and over thousands of steps on fine grids the exact adjoint then grows without
+ * bound while finite differences of the forward run stay finite.  Errors:
+ * CDBM_EINVAL for b outside [0, 1] or non-finite. */
+cdbm_status cdbm_adjoint_set_tie_band(cdbm_ctx *ctx, double band);
+
 /* fbar = (d(rho, u_x, u_y, T)/df)^T (rho_bar, ux_bar, uy_bar, T_bar) at the current
  * state (the read-out of cdbm_macros transposed); NULL cotangents count as zero. */
 cdbm_status cdbm_macros_vjp(cdbm_ctx *ctx, const double *rho_bar, const double *ux_bar, const double *uy_bar,

@@ -14,6 +14,17 @@
 //   base_bar = a_base o,   tau_bar = sum o . d out / d tau = -sum o . (heq - gamma h g) / tau.
 // minmod is piecewise linear; its derivative is that of the branch the forward pass
 // took (1 for the chosen argument, 0 for the other, 0 when the result is 0; X on a tie).
+// With a tie band b > 0, arguments of one sign whose magnitudes differ by less than
+// b max(|X|, |Y|) share the derivative by a linear ramp,
+//   w_X = (1 + t) / 2,  w_Y = (1 - t) / 2,  t = clamp((|Y| - |X|) / (b max(|X|, |Y|)), -1, 1),
+// which is the exact branch derivative outside the band and the midpoint of minmod's
+// generalised gradient at a tie.  The frozen-branch derivative (b = 0) is the exact
+// derivative of the discrete step, but where the limiter switches between nearly
+// equal slopes its linearisation can be anti-diffusive (a downwind pick beside an
+// upwind one gives Re D(theta) = -cos(theta) (1 - cos(theta)) for the transport
+// symbol), so over thousands of steps on fine grids the exact adjoint can grow
+// without bound; the band replaces those picks by their average (a dissipative,
+// Fromm-type linearisation).
 #include "cdbm_device.cuh"
 
 namespace cdbm {
@@ -31,6 +42,23 @@ __device__ __forceinline__ int minmod_branch(double X, double Y)
     const bool x_le_y = (ahx < ahy) | ((ahx == ahy) & ((unsigned)lx <= (unsigned)ly));
     const bool keep = ((hx ^ hy) >= 0) & ((ahx | (unsigned)lx) != 0u) & ((ahy | (unsigned)ly) != 0u);
     return keep ? (x_le_y ? 1 : 2) : 0;
+}
+
+// Weights (w_X, w_Y) of the derivative of minmod(X, Y) with tie band `band` (see the
+// header comment); band == 0 gives the branch derivative exactly.
+__device__ __forceinline__ void minmod_weights(double X, double Y, double band, double &wx, double &wy)
+{
+    const int b = minmod_branch(X, Y);
+    if (b == 0 || band <= 0.0) {
+        wx = b == 1 ? 1.0 : 0.0;
+        wy = b == 2 ? 1.0 : 0.0;
+        return;
+    }
+    const double ax = fabs(X), ay = fabs(Y);
+    double t = (ay - ax) / (band * fmax(ax, ay));
+    t = fmin(1.0, fmax(-1.0, t));
+    wx = 0.5 * (1.0 + t);
+    wy = 0.5 * (1.0 - t);
 }
 
 struct MomBar {
@@ -152,21 +180,24 @@ __device__ __forceinline__ MomBar equilibrium_vjp(const EqBlocks &B, const Model
 // m-2s .. m+2s (gm2 .. gp2 in upwind order: gm2 = g_{m-2s}, ..., gp2 = g_{m+2s}) and
 // the cotangent o at m-s .. m+2s.
 __device__ __forceinline__ double flux_vjp(double l, double gm2, double gm1, double g0, double gp1, double gp2,
-                                           double om1, double o0, double op1, double op2)
+                                           double om1, double o0, double op1, double op2, double band)
 {
     // U_k = g_k - g_{k-s} at k = m-s, m, m+s, m+2s
     const double Um1 = gm1 - gm2, U0 = g0 - gm1, Up1 = gp1 - g0, Up2 = gp2 - gp1;
-    // N_k = minmod(U_{k+s}, U_k): branch 1 picks U_{k+s}, branch 2 picks U_k
-    const int bm1 = minmod_branch(U0, Um1), b0 = minmod_branch(Up1, U0), bp1 = minmod_branch(Up2, Up1);
+    // N_k = minmod(U_{k+s}, U_k): weight X on U_{k+s}, weight Y on U_k
+    double xm1, ym1, x0, y0, xp1, yp1;
+    minmod_weights(U0, Um1, band, xm1, ym1);
+    minmod_weights(Up1, U0, band, x0, y0);
+    minmod_weights(Up2, Up1, band, xp1, yp1);
     // N_bar_k = (l / 2) (o_{k+s} - o_k)  (from -l D_k and +l D_{k+s} / 2 ... see header)
     const double hl = 0.5 * l;
     const double Nbm1 = hl * (o0 - om1), Nb0 = hl * (op1 - o0), Nbp1 = hl * (op2 - op1);
-    // U_bar_k = -l o_k + [branch_{k-s} == 1] N_bar_{k-s} + [branch_k == 2] N_bar_k
+    // U_bar_k = -l o_k + w_X(N_{k-s}) N_bar_{k-s} + w_Y(N_k) N_bar_k
     double Ub0 = -l * o0, Ubp1 = -l * op1;
-    if (bm1 == 1) Ub0 += Nbm1;
-    if (b0 == 2) Ub0 += Nb0;
-    if (b0 == 1) Ubp1 += Nb0;
-    if (bp1 == 2) Ubp1 += Nbp1;
+    Ub0 = fma(xm1, Nbm1, Ub0);
+    Ub0 = fma(y0, Nb0, Ub0);
+    Ubp1 = fma(x0, Nb0, Ubp1);
+    Ubp1 = fma(yp1, Nbp1, Ubp1);
     // U_k = g_k - g_{k-s}: g_bar_m = U_bar_m - U_bar_{m+s}
     return Ub0 - Ubp1;
 }
@@ -178,7 +209,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_stage_kernel(const double
                                                                     const double *prev, double c_prev,
                                                                     double *out_bar, const StageArgs a,
                                                                     double gamma_h, double inv_tau,
-                                                                    double *tau_acc)
+                                                                    double band, double *tau_acc)
 {
     __shared__ double red[kAdjThreads];
     const int nx = a.nx, ny = a.ny;
@@ -231,7 +262,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_stage_kernel(const double
                 const double gm2 = gp[row + xs[2 - 2 * s]], gm1 = gp[row + xs[2 - s]];
                 const double gp1 = gp[row + xs[2 + s]], gp2 = gp[row + xs[2 + 2 * s]];
                 const double om1 = op[row + xs[2 - s]], op1 = op[row + xs[2 + s]], op2 = op[row + xs[2 + 2 * s]];
-                gb += flux_vjp(a.lx[grp], gm2, gm1, f[i], gp1, gp2, om1, o[i], op1, op2);
+                gb += flux_vjp(a.lx[grp], gm2, gm1, f[i], gp1, gp2, om1, o[i], op1, op2, band);
             }
             if (diry(i) != 0 && ny > 1) {
                 const int s = diry(i);
@@ -239,7 +270,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_stage_kernel(const double
                 const double gp1 = gp[(size_t)ys[2 + s] * nx + x], gp2 = gp[(size_t)ys[2 + 2 * s] * nx + x];
                 const double om1 = op[(size_t)ys[2 - s] * nx + x], op1 = op[(size_t)ys[2 + s] * nx + x];
                 const double op2 = op[(size_t)ys[2 + 2 * s] * nx + x];
-                gb += flux_vjp(a.ly[grp], gm2, gm1, f[i], gp1, gp2, om1, o[i], op1, op2);
+                gb += flux_vjp(a.ly[grp], gm2, gm1, f[i], gp1, gp2, om1, o[i], op1, op2, band);
             }
             if (prev) gb = fma(c_prev, prev[i * P + c], gb);
             out_bar[i * P + c] = gb;
@@ -333,10 +364,10 @@ dim3 adjoint_grid(int nx, int ny) { return dim3((nx + kAdjThreads - 1) / kAdjThr
 
 cudaError_t launch_adjoint_stage(const double *g, const double *ob, const double *prev, double c_prev,
                                  double *out_bar, const StageArgs &a, double gamma_h, double inv_tau,
-                                 double *tau_acc, cudaStream_t s)
+                                 double band, double *tau_acc, cudaStream_t s)
 {
     adjoint_stage_kernel<<<adjoint_grid(a.nx, a.ny), kAdjThreads, 0, s>>>(g, ob, prev, c_prev, out_bar, a, gamma_h,
-                                                                          inv_tau, tau_acc);
+                                                                          inv_tau, band, tau_acc);
     return cudaGetLastError();
 }
 

@@ -1,16 +1,26 @@
 // Double-float ("df64") arithmetic on the FP32 pipe for the CDBM_FP32_DF64 state.
 //
-// A value is an unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2,
-// i.e. about 48 significant bits.  The operations are built from the classical
-// error-free transformations: TwoSum (Knuth) for the exact rounding error of a
-// sum, Fast-TwoSum (Dekker) when the larger operand is known, and the FMA-based
-// TwoProduct for the exact error of a product.  Sums use the accurate variant
-// (both pairs of parts combined through TwoSum, renormalised twice), which keeps
-// a relative error of a few 2^-48 also under cancellation.
+// A value is an unevaluated sum hi + lo of two floats, about 48 significant bits.
+// The operations are built from the classical error-free transformations: TwoSum
+// (Knuth) for the exact rounding error of a sum, Fast-TwoSum (Dekker) when the
+// larger operand is known, and the FMA-based TwoProduct for the exact error of a
+// product.
+//
+// Error model.  Every quantity of the stage equilibrium is at most of the size of
+// the reference equilibrium F (the moments of f, their products with O(1) block
+// coefficients), and what must be accurate is the *absolute* error, against the
+// single-precision deviation g = f - F the result is rounded to.  So the sums use
+// the cheap ("sloppy") double-float addition, whose error is a few 2^-48 of its
+// operands rather than of its result, and products are left unnormalised (the low
+// part may reach a few ulp of the high part); both keep the absolute error of every
+// quantity at a few 2^-47 of F, i.e. below 1/100 ulp of any deviation larger than
+// about 2^-17 F.  Cancellation against F is harmless under this model: it only
+// makes the final rounding to float relative to the smaller deviation.
 //
 // On GB300 the FP64 pipe runs 1/64 of the FP32 rate, so moving the equilibrium of
-// the single-precision state from double to df64 trades each FP64 instruction for
-// 3-20 FP32 instructions that the four FP32 issue slots per SM absorb.
+// the single-precision state from double to double-float trades each FP64
+// instruction for 4-15 FP32 instructions that the four FP32 issue slots per SM
+// absorb.
 #pragma once
 
 #include "cdbm_device.cuh"
@@ -27,7 +37,7 @@ __host__ __device__ inline df df_from(double v)
 
 __device__ __forceinline__ df df_of(float v) { return {v, 0.0f}; }
 
-__device__ __forceinline__ float df_to_float(df x) { return x.hi + x.lo; }
+__device__ __forceinline__ float df_to_float(df x) { return __fadd_rn(x.hi, x.lo); }
 
 // s + e = a + b exactly.
 __device__ __forceinline__ df two_sum(float a, float b)
@@ -46,27 +56,26 @@ __device__ __forceinline__ df fast_two_sum(float a, float b)
     return {s, e};
 }
 
+// x + y with an error of a few 2^-48 (|x| + |y|): exact sum of the high parts, the
+// low parts added in float, renormalised once.
 __device__ __forceinline__ df df_add(df x, df y)
 {
-    df s = two_sum(x.hi, y.hi);
-    const df t = two_sum(x.lo, y.lo);
-    s.lo = __fadd_rn(s.lo, t.hi);
-    s = fast_two_sum(s.hi, s.lo);
-    s.lo = __fadd_rn(s.lo, t.lo);
-    return fast_two_sum(s.hi, s.lo);
+    const df s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, __fadd_rn(__fadd_rn(x.lo, y.lo), s.lo));
 }
 
 __device__ __forceinline__ df df_neg(df x) { return {-x.hi, -x.lo}; }
 __device__ __forceinline__ df df_sub(df x, df y) { return df_add(x, df_neg(y)); }
 
-// x * y with the x.lo * y.lo term dropped (below the df64 rounding).
+// x * y, unnormalised: the exact error of hi * hi plus the cross terms (x.lo * y.lo
+// is below the df rounding and dropped).
 __device__ __forceinline__ df df_mul(df x, df y)
 {
     const float p = __fmul_rn(x.hi, y.hi);
     float e = __fmaf_rn(x.hi, y.hi, -p);
     e = __fmaf_rn(x.hi, y.lo, e);
     e = __fmaf_rn(x.lo, y.hi, e);
-    return fast_two_sum(p, e);
+    return {p, e};
 }
 
 __device__ __forceinline__ df df_fma(df a, df b, df c) { return df_add(df_mul(a, b), c); }
@@ -144,7 +153,7 @@ __device__ __forceinline__ void df_equilibrium(const DFBlocks &B, const DFModel 
     const df T = df_mul(P, r);
     if (!(positive_finite_f(rho.hi) && positive_finite_f(P.hi))) atomicOr(flag, kFlagNonPhys);
 
-    const df ux2 = df_mul(ux, ux), uy2 = df_mul(uy, uy), u2 = df_add(ux2, uy2);
+    const df ux2 = df_mul(ux, ux), uy2 = df_mul(uy, uy), u2 = df_add(ux2, uy2), du2 = df_sub(ux2, uy2);
     const df m1416 = df_fma(T, df_fma(d.Kp6, ru2, df_mul(d.twoKp2, P)), df_mul(ru2, u2));
     const df W4 = df_fma(d.Kp4, T, u2);
     const df d57 = df_sub(df_mul(jx, ux), jyuy);
@@ -152,11 +161,15 @@ __device__ __forceinline__ void df_equilibrium(const DFBlocks &B, const DFModel 
     float c0[4], cx[4], cy[4];
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
-        const df *S = B.S + 4 * g, *V = B.V + 4 * g;
-        df s = df_fma(S[3], m1416, df_fma(S[2], ru2, df_fma(S[1], E, df_mul(S[0], rho))));
+        const df *S = B.S + 4 * g;
+        const df s = df_fma(S[3], m1416, df_fma(S[2], ru2, df_fma(S[1], E, df_mul(S[0], rho))));
         c0[g] = df_to_float(df_sub(s, R.sF[g]));
-        cx[g] = df_to_float(df_mul(jx, df_fma(V[3], T, df_fma(V[2], uy2, df_fma(V[1], ux2, V[0])))));
-        cy[g] = df_to_float(df_mul(jy, df_fma(V[3], T, df_fma(V[1], uy2, df_fma(V[2], ux2, V[0])))));
+        // V0 + V1 u_x^2 + V2 u_y^2 + V3 T and its mirror, through the shared part
+        // V0 + V3 T + (V1 + V2)/2 u^2 and the odd part (V1 - V2)/2 (u_x^2 - u_y^2)
+        const df cm = df_fma(B.Vs[g], u2, df_fma(B.V3[g], T, B.V0[g]));
+        const df cd = df_mul(B.Vd[g], du2);
+        cx[g] = df_to_float(df_mul(jx, df_add(cm, cd)));
+        cy[g] = df_to_float(df_mul(jy, df_sub(cm, cd)));
     }
     const float dqa = df_to_float(df_mul(d57, df_fma(B.B1[1], W4, B.B1[0])));
     const float dqc = df_to_float(df_mul(d57, df_fma(B.B1[3], W4, B.B1[2])));

@@ -51,8 +51,9 @@ struct ModelConsts {
 struct DFPair {
     float hi, lo;
 };
-struct DFBlocks {                 // EqBlocks (scaled per stage)
-    DFPair S[16], V[16], B1[4], B2[4];
+struct DFBlocks {                 // EqBlocks (scaled per stage); the x-odd rows of V as
+    DFPair S[16], B1[4], B2[4];   // V0, V3, (V1 + V2)/2 and (V1 - V2)/2 per group
+    DFPair V0[4], V3[4], Vs[4], Vd[4];
 };
 struct DFModel {                  // the ModelConsts the equilibrium uses
     DFPair c[4], w[4];
@@ -145,10 +146,11 @@ cudaError_t launch_stage(const StageLaunch &L, const void *g, const void *base, 
                          const StageArgs &a, unsigned *flag, cudaStream_t s);
 
 // ---- adjoint kernels (cdbm_adjoint.cu), double precision, periodic axes ----
-// out_bar = c_prev * prev + (stage VJP at g applied to ob); tau_acc[block] += tau term.
+// out_bar = c_prev * prev + (stage VJP at g applied to ob); tau_acc[block] += tau term;
+// band: tie band of the limiter derivative (0: the exact branch derivative).
 cudaError_t launch_adjoint_stage(const double *g, const double *ob, const double *prev, double c_prev,
                                  double *out_bar, const StageArgs &a, double gamma_h, double inv_tau,
-                                 double *tau_acc, cudaStream_t s);
+                                 double band, double *tau_acc, cudaStream_t s);
 dim3 adjoint_grid(int nx, int ny);
 cudaError_t launch_init_vjp(const FieldArgs &a, const double *f0, const double *fbar, double *rho_bar,
                             double *ux_bar, double *uy_bar, double *T_bar, cudaStream_t s);

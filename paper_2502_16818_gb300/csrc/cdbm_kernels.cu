@@ -542,13 +542,15 @@ StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count
 DFBlocks df_blocks(const EqBlocks &e)
 {
     DFBlocks d;
-    for (int k = 0; k < 16; ++k) {
-        d.S[k] = df_from(e.S[k]);
-        d.V[k] = df_from(e.V[k]);
-    }
+    for (int k = 0; k < 16; ++k) d.S[k] = df_from(e.S[k]);
     for (int k = 0; k < 4; ++k) {
         d.B1[k] = df_from(e.B1[k]);
         d.B2[k] = df_from(e.B2[k]);
+        const double *V = e.V + 4 * k;
+        d.V0[k] = df_from(V[0]);
+        d.V3[k] = df_from(V[3]);
+        d.Vs[k] = df_from(0.5 * (V[1] + V[2]));
+        d.Vd[k] = df_from(0.5 * (V[1] - V[2]));
     }
     return d;
 }
