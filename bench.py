@@ -47,8 +47,8 @@ FP64_LANES_PER_CLK_PER_SM = 2       # 1.25 TFLOP/s nominal FP64 / (2 flops x 152
 # the stage kernels; valid only while the kernel sources hash to TRAFFIC_SHA.
 # Captured at 1024^2 (134 MB per plane set, above L2) and scaled by 16 cells-fold; see
 # profiles/stage_kernel_tgv.md.
-TRAFFIC_SHA = "4a03d10916753b49"
-TRAFFIC_BYTES_PER_LAUNCH = 5.097e9
+TRAFFIC_SHA = "38a1cf4a1024f862"
+TRAFFIC_BYTES_PER_LAUNCH = 5.098e9
 
 
 STAGE_SOURCES = ("cdbm_device.cuh", "cdbm_kernels.cu", "cdbm_internal.h")
@@ -76,6 +76,7 @@ def parse():
     p.add_argument("--no-variants", action="store_true", help="skip the FP32-bulk and ensemble runs")
     p.add_argument("--ens-steps", type=int, default=200, help="timed steps of the tube ensemble")
     p.add_argument("--no-ensemble", action="store_true", help="skip the tube ensemble runs")
+    p.add_argument("--no-configs", action="store_true", help="skip the per-configuration wall times")
     p.add_argument("--adj-steps", type=int, default=4000, help="steps of the adjoint run (0: skip it)")
     p.add_argument("--adj-every", type=int, default=200, help="checkpoint interval of the adjoint run")
     p.add_argument("--adj-n", type=int, default=1024, help="grid size of the adjoint run")
@@ -241,7 +242,7 @@ def run_cdbm(a, rank, world, local_rank):
         dist.barrier()
     ms_max = replicas.max_over_ranks(ms, device="cuda")
     value = replicas.job_throughput(cells * a.steps, world, ms_max * 1e-3)
-    rho64, ux64, _, T64 = s.macros()
+    rho64, ux64, uy64, T64 = s.macros()
     amp1 = tgv_amplitude(w, ux64)
     t_run = a.steps * w.dt
     nu = float(T64.mean()) * w.tau
@@ -282,26 +283,43 @@ def run_cdbm(a, rank, world, local_rank):
     s.close()
 
     if not a.no_variants and rank == 0:
-        out["fp32_bulk"] = fp32_variant(a, w, torch, Solver, CDBM_FP32_BULK, rho64, value, amp0,
+        out["fp32_bulk"] = fp32_variant(a, w, torch, Solver, CDBM_FP32_BULK, (rho64, ux64, uy64, T64), value, amp0,
                                         "f in single precision as deviation from a reference "
                                         "equilibrium; sums, moment shift and equilibrium product in double")
-        out["fp32_df64"] = fp32_variant(a, w, torch, Solver, CDBM_FP32_DF64, rho64, value, amp0,
+        out["fp32_df64"] = fp32_variant(a, w, torch, Solver, CDBM_FP32_DF64, (rho64, ux64, uy64, T64), value, amp0,
                                         "as fp32_bulk, with sums, moment shift and equilibrium product in "
                                         "double-float arithmetic on the FP32 pipe")
         if not a.no_ensemble:
             out["ensemble"] = ensemble(a, torch)
         if a.adj_steps > 0:
             out["adjoint"] = adjoint(a, torch)
-        out["configs"] = configs(a, torch)
+        if not a.no_configs:
+            out["configs"] = configs(a, torch)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, side=min(2048, w.nx))
     if rank == 0:
         print(json.dumps(out), flush=True)
 
 
-def fp32_variant(a, w, torch, Solver, precision, rho64, value64, amp0, note):
+def field_errors(got, ref, gamma, torch):
+    """Per-field errors of (rho, ux, uy, T) against a reference run: relative L2 and
+    max-norm of rho and T, velocity max-norm over max(|u|, c_s)."""
+    rho, ux, uy, T = got
+    r_rho, r_ux, r_uy, r_T = ref
+    cs = float(torch.sqrt(gamma * r_T.mean()))
+    us = max(float(r_ux.abs().max()), float(r_uy.abs().max()), cs)
+    return {"rho_l2": float(torch.linalg.norm(rho - r_rho) / torch.linalg.norm(r_rho)),
+            "rho_max": float((rho - r_rho).abs().max() / r_rho.abs().max()),
+            "T_l2": float(torch.linalg.norm(T - r_T) / torch.linalg.norm(r_T)),
+            "T_max": float((T - r_T).abs().max() / r_T.abs().max()),
+            "u_max_over_scale": max(float((ux - r_ux).abs().max()), float((uy - r_uy).abs().max())) / us}
+
+
+def fp32_variant(a, w, torch, Solver, precision, ref64, value64, amp0, note):
     """A single-precision state on the same vortex and steps: throughput, speed-up over
-    the FP64 plain path, relative L2 density error against the FP64 run, decay rate."""
+    the FP64 plain path, per-field errors against the FP64 run, decay rate."""
+    from paper_2502_16818_gb300 import workloads as W
+    rho64 = ref64[0]
     import numpy as np
     s, stream, _ = time_tgv(w, precision, a.steps, a.warmup, torch, Solver)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -311,13 +329,14 @@ def fp32_variant(a, w, torch, Solver, precision, rho64, value64, amp0, note):
     e1.synchronize()
     ms = e0.elapsed_time(e1)
     s.sync()
-    rho, ux, _, T = s.macros()
+    rho, ux, uy, T = s.macros()
     s.close()
     l2 = float(torch.linalg.norm(rho - rho64) / torch.linalg.norm(rho64))
+    errs = field_errors((rho, ux, uy, T), ref64, W.gamma_of(w.I), torch)
     val = w.nx * w.ny * a.steps / (ms * 1e-3)
     amp1 = tgv_amplitude(w, ux)
     return {"value": val, "unit": UNIT, "ms_per_step": ms / a.steps, "speedup_vs_fp64": val / value64,
-            "l2_density_error_vs_fp64": l2, "steps_compared": a.steps + a.warmup,
+            "l2_density_error_vs_fp64": l2, "field_errors_vs_fp64": errs, "steps_compared": a.steps + a.warmup,
             "decay_rate_measured": float(-np.log(amp1 / amp0) / (a.steps * w.dt)),
             "hbm_gbs": 320 * w.nx * w.ny * a.steps / (ms * 1e-3) / 1e9, "note": note}
 
@@ -410,8 +429,9 @@ def adjoint(a, torch):
     """Gradient of L = sum (rho_T - rho_target)^2 with respect to the initial rho, T
     (and u) fields and tau on the periodic sound-mode case: forward run storing a
     checkpoint every `every` steps, then the reverse sweep (segment recomputation
-    and the adjoint stage kernels).  Throughput counts the forward cell-updates over
-    the time of forward plus backward."""
+    and the adjoint stage kernels), with the frozen limiter linearisation (the exact
+    one grows without bound over this horizon).  Throughput counts the forward
+    cell-updates over the time of forward plus backward."""
     from paper_2502_16818_gb300 import Solver, cdbm, workloads as W
     w = W.sound_modes(n=a.adj_n, seed=0, kmax=8, steps=a.adj_steps)
     target = torch.from_numpy(W.sound_modes(n=a.adj_n, seed=1, kmax=8).rho).to("cuda")
@@ -419,6 +439,7 @@ def adjoint(a, torch):
     with torch.cuda.stream(st):
         s = Solver.from_workload(w, stream=st)
         s.init(*(torch.from_numpy(x).to("cuda") for x in (w.rho, w.ux, w.uy, w.T)))
+        cdbm.cdbm_adjoint_set_limiter(s.ctx, cdbm.CDBM_ADJ_LIMITER_FROZEN)
         grads = [torch.empty((w.ny, w.nx), dtype=torch.float64, device="cuda") for _ in range(4)]
         fbar = torch.empty((16, w.ny, w.nx), dtype=torch.float64, device="cuda")
     s.sync()
@@ -442,7 +463,7 @@ def adjoint(a, torch):
     cells = w.nx * w.ny
     return {"value": cells * a.adj_steps / ((fwd_ms + bwd_ms) * 1e-3), "unit": UNIT,
             "workload": "sound_modes_%dx%d_kmax8_fp64" % (w.nx, w.ny), "steps": a.adj_steps,
-            "checkpoint_every": a.adj_every, "forward_ms": fwd_ms, "backward_ms": bwd_ms,
+            "checkpoint_every": a.adj_every, "limiter": "frozen", "forward_ms": fwd_ms, "backward_ms": bwd_ms,
             "backward_over_forward": bwd_ms / fwd_ms, "wall_s": wall, "loss": loss, "dL_dtau": gtau,
             "grad_rho_l2": float(torch.linalg.norm(grads[0])), "grad_T_l2": float(torch.linalg.norm(grads[3])),
             "checkpoint_bytes": 128 * cells * (a.adj_steps // a.adj_every + 1)}

@@ -200,19 +200,26 @@ cdbm_status cdbm_adjoint_forward(cdbm_ctx *ctx, int nsteps, int every);
 cdbm_status cdbm_adjoint_backward(cdbm_ctx *ctx, const double *fbar, double *grad_rho, double *grad_ux,
                                   double *grad_uy, double *grad_T, double *grad_tau);
 
-/* Tie band b of the limiter derivative used by cdbm_adjoint_backward, 0 <= b <= 1
- * (default 0).  With b = 0 the limiter enters through the derivative of the branch
- * the forward pass took, i.e. the adjoint is the exact derivative of the discrete
- * step.  With b > 0, two same-signed minmod arguments whose magnitudes differ by
- * less than b max(|X|, |Y|) share the derivative on a linear ramp,
- * w_X = (1 + t)/2, w_Y = 1 - w_X, t = clamp((|Y| - |X|) / (b max(|X|, |Y|)), -1, 1);
- * outside the band the branch derivative is used unchanged.  This is a
- * regularisation, not part of the paper's scheme (Eqs. 12-20): where the limiter
- * picks between nearly equal slopes the exact linearisation can be anti-diffusive,
- * and over thousands of steps on fine grids the exact adjoint then grows without
- * bound while finite differences of the forward run stay finite.  Errors:
- * CDBM_EINVAL for b outside [0, 1] or non-finite. */
-cdbm_status cdbm_adjoint_set_tie_band(cdbm_ctx *ctx, double band);
+/* Linearisation of the minmod limiter N = minmod(U_{k+s}, U_k) (Eq. 16) used by
+ * cdbm_adjoint_backward.  EXACT is the derivative of the branch the forward pass
+ * took, i.e. the exact derivative of the discrete step.  Where the limiter picks the
+ * downwind slope beside an upwind pick, that linearisation is anti-diffusive, and on
+ * fine grids over thousands of steps the exact adjoint can grow without bound while
+ * finite differences of the forward run stay finite (the forward map is then rough
+ * at perturbations below ~1e-5).  The two frozen modes are the usual approximate
+ * linearisations for that regime: FROZEN_RATIO holds the limiter value
+ * phi = N / U_k in [0, 1] fixed (dN = phi dU_k); FROZEN holds N fixed (dN = 0, a
+ * first-order upwind linearisation of the transport).  Neither is part of the
+ * paper's scheme; they trade exactness for a bounded adjoint. */
+typedef enum {
+    CDBM_ADJ_LIMITER_EXACT = 0,
+    CDBM_ADJ_LIMITER_FROZEN_RATIO = 1,
+    CDBM_ADJ_LIMITER_FROZEN = 2
+} cdbm_adj_limiter;
+
+/* Selects the limiter linearisation (default CDBM_ADJ_LIMITER_EXACT).  Errors:
+ * CDBM_EINVAL for an unknown mode. */
+cdbm_status cdbm_adjoint_set_limiter(cdbm_ctx *ctx, int mode);
 
 /* fbar = (d(rho, u_x, u_y, T)/df)^T (rho_bar, ux_bar, uy_bar, T_bar) at the current
  * state (the read-out of cdbm_macros transposed); NULL cotangents count as zero. */
@@ -261,8 +268,9 @@ cdbm_status cdbm_batch_init(cdbm_batch *b, const double *rho, const double *ux, 
  * CUDA graph.  Asynchronous; cdbm_batch_sync reports a non-physical state. */
 cdbm_status cdbm_batch_step(cdbm_batch *b, int nsteps);
 
-/* Times the candidate tiles (64/128/256 threads per block x 1-4 blocks per SM, each
- * with its own longest-first partition of the tubes) over trial_steps steps, keeps
+/* Times the candidate tiles (64/128/256 threads per block x 1, 2, 3, 4 or 6 blocks
+ * per SM, at most 1024 threads per SM, 1536 for CDBM_FP32_DF64; each with its own
+ * longest-first partition of the tubes) over trial_steps steps, keeps
  * the fastest and reports it.  The state is saved before and restored after the
  * trials, and results do not depend on the tile. */
 cdbm_status cdbm_batch_autotune(cdbm_batch *b, int trial_steps, int *threads, int *blocks_per_sm);

@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "CDBM_OK", 1: "CDBM_EINVAL", 2: "CDBM_ESINGULAR", 3: "CDBM_EN
                 4: "CDBM_ECUDA", 5: "CDBM_ENONPHYS", 6: "CDBM_ETIMEOUT"}
 CDBM_BC_PERIODIC, CDBM_BC_ZEROGRAD = 0, 1
 CDBM_FP64, CDBM_FP32_BULK, CDBM_FP32_DF64 = 0, 1, 2
+CDBM_ADJ_LIMITER_EXACT, CDBM_ADJ_LIMITER_FROZEN_RATIO, CDBM_ADJ_LIMITER_FROZEN = 0, 1, 2
 CDBM_RK2_TVD, CDBM_RK2_MIDPOINT = 0, 1
 
 #: every entry point declared in include/cdbm.h
@@ -30,7 +31,7 @@ EXPORTS = ("cdbm_create", "cdbm_set_rk", "cdbm_init", "cdbm_step", "cdbm_macros"
            "cdbm_batch_create", "cdbm_batch_init", "cdbm_batch_step", "cdbm_batch_autotune",
            "cdbm_batch_set_tile", "cdbm_batch_macros", "cdbm_batch_info", "cdbm_batch_sync",
            "cdbm_batch_last_error", "cdbm_batch_destroy", "cdbm_adjoint_forward",
-           "cdbm_adjoint_backward", "cdbm_adjoint_set_tie_band", "cdbm_macros_vjp")
+           "cdbm_adjoint_backward", "cdbm_adjoint_set_limiter", "cdbm_macros_vjp")
 CDBM_NOALLOC_MAX_CELLS = 32768
 
 
@@ -111,7 +112,7 @@ def load(path: str | None = None):
         "cdbm_batch_destroy": ([ctx], None),
         "cdbm_adjoint_forward": ([ctx, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "cdbm_adjoint_backward": ([ctx, _vp, _vp, _vp, _vp, _vp, _dp], ctypes.c_int),
-        "cdbm_adjoint_set_tie_band": ([ctx, ctypes.c_double], ctypes.c_int),
+        "cdbm_adjoint_set_limiter": ([ctx, ctypes.c_int], ctypes.c_int),
         "cdbm_macros_vjp": ([ctx, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -234,9 +235,9 @@ def cdbm_adjoint_backward(ctx, fbar, grad_rho=0, grad_ux=0, grad_uy=0, grad_T=0)
     return gt.value
 
 
-def cdbm_adjoint_set_tie_band(ctx, band):
+def cdbm_adjoint_set_limiter(ctx, mode):
     lib = load()
-    _check(lib, ctx, lib.cdbm_adjoint_set_tie_band(ctx, float(band)))
+    _check(lib, ctx, lib.cdbm_adjoint_set_limiter(ctx, int(mode)))
 
 
 def cdbm_macros_vjp(ctx, rho_bar, ux_bar, uy_bar, T_bar, fbar):
@@ -516,16 +517,17 @@ def make_run_function():
         """(rho, u_x, u_y, T) at the end of `nsteps` steps from initial fields
         (rho0, ux0, uy0, T0) and relaxation time tau; `spec` holds the remaining run
         parameters (nx, ny, dx, dy, dt, I, vg, eg; periodic axes; optional
-        tie_band, see cdbm_adjoint_set_tie_band).  The backward pass runs the
-        adjoint kernels with a checkpoint every `every` steps."""
+        limiter, a CDBM_ADJ_LIMITER_* mode of cdbm_adjoint_set_limiter).  The
+        backward pass runs the adjoint kernels with a checkpoint every `every`
+        steps."""
 
         @staticmethod
         def forward(ctx, rho0, ux0, uy0, T0, tau, spec, nsteps, every):
             s = Solver(spec["nx"], spec["ny"], spec["dx"], spec["dy"], spec["dt"], float(tau), spec["I"],
                        spec["vg"], spec["eg"])
             s.init(rho0.detach(), ux0.detach(), uy0.detach(), T0.detach())
-            if spec.get("tie_band", 0.0):
-                cdbm_adjoint_set_tie_band(s.ctx, spec["tie_band"])
+            if spec.get("limiter", CDBM_ADJ_LIMITER_EXACT) != CDBM_ADJ_LIMITER_EXACT:
+                cdbm_adjoint_set_limiter(s.ctx, spec["limiter"])
             cdbm_adjoint_forward(s.ctx, nsteps, every)
             out = s.macros()
             ctx.solver = s

@@ -14,17 +14,17 @@
 //   base_bar = a_base o,   tau_bar = sum o . d out / d tau = -sum o . (heq - gamma h g) / tau.
 // minmod is piecewise linear; its derivative is that of the branch the forward pass
 // took (1 for the chosen argument, 0 for the other, 0 when the result is 0; X on a tie).
-// With a tie band b > 0, arguments of one sign whose magnitudes differ by less than
-// b max(|X|, |Y|) share the derivative by a linear ramp,
-//   w_X = (1 + t) / 2,  w_Y = (1 - t) / 2,  t = clamp((|Y| - |X|) / (b max(|X|, |Y|)), -1, 1),
-// which is the exact branch derivative outside the band and the midpoint of minmod's
-// generalised gradient at a tie.  The frozen-branch derivative (b = 0) is the exact
-// derivative of the discrete step, but where the limiter switches between nearly
-// equal slopes its linearisation can be anti-diffusive (a downwind pick beside an
-// upwind one gives Re D(theta) = -cos(theta) (1 - cos(theta)) for the transport
-// symbol), so over thousands of steps on fine grids the exact adjoint can grow
-// without bound; the band replaces those picks by their average (a dissipative,
-// Fromm-type linearisation).
+// That is the exact derivative of the discrete step (CDBM_ADJ_LIMITER_EXACT).  Two
+// approximate linearisations are available for long horizons on fine grids, where
+// the exact one can grow without bound: where the limiter picks the downwind slope
+// beside an upwind pick its linearisation is anti-diffusive (for the transport
+// symbol, Re D(theta) = -cos(theta) (1 - cos(theta)) if that pattern were uniform),
+// and over thousands of steps these picks amplify the adjoint while finite
+// differences of the forward run stay finite.
+//   CDBM_ADJ_LIMITER_FROZEN_RATIO: the limiter value phi = N_k / U_k in [0, 1] is held
+//     fixed, dN_k = phi dU_k (the downwind dependence is dropped);
+//   CDBM_ADJ_LIMITER_FROZEN: the limiter output is held fixed, dN_k = 0 (the
+//     linearisation is first-order upwind transport).
 #include "cdbm_device.cuh"
 
 namespace cdbm {
@@ -44,21 +44,21 @@ __device__ __forceinline__ int minmod_branch(double X, double Y)
     return keep ? (x_le_y ? 1 : 2) : 0;
 }
 
-// Weights (w_X, w_Y) of the derivative of minmod(X, Y) with tie band `band` (see the
-// header comment); band == 0 gives the branch derivative exactly.
-__device__ __forceinline__ void minmod_weights(double X, double Y, double band, double &wx, double &wy)
+// Weights (w_X, w_Y) of the linearised minmod(X, Y) = N for the limiter mode kMode.
+template <int kMode>
+__device__ __forceinline__ void minmod_weights(double X, double Y, double &wx, double &wy)
 {
     const int b = minmod_branch(X, Y);
-    if (b == 0 || band <= 0.0) {
+    if (kMode == CDBM_ADJ_LIMITER_EXACT) {
         wx = b == 1 ? 1.0 : 0.0;
         wy = b == 2 ? 1.0 : 0.0;
-        return;
+    } else if (kMode == CDBM_ADJ_LIMITER_FROZEN_RATIO) {
+        wx = 0.0;
+        wy = b == 1 ? X * rcp64(fabs(Y)) * (Y < 0.0 ? -1.0 : 1.0) : (b == 2 ? 1.0 : 0.0);
+    } else {
+        wx = 0.0;
+        wy = 0.0;
     }
-    const double ax = fabs(X), ay = fabs(Y);
-    double t = (ay - ax) / (band * fmax(ax, ay));
-    t = fmin(1.0, fmax(-1.0, t));
-    wx = 0.5 * (1.0 + t);
-    wy = 0.5 * (1.0 - t);
 }
 
 struct MomBar {
@@ -179,16 +179,17 @@ __device__ __forceinline__ MomBar equilibrium_vjp(const EqBlocks &B, const Model
 // cell m from the terms -l D_j of the cells j whose stencil contains m, given g at
 // m-2s .. m+2s (gm2 .. gp2 in upwind order: gm2 = g_{m-2s}, ..., gp2 = g_{m+2s}) and
 // the cotangent o at m-s .. m+2s.
+template <int kMode>
 __device__ __forceinline__ double flux_vjp(double l, double gm2, double gm1, double g0, double gp1, double gp2,
-                                           double om1, double o0, double op1, double op2, double band)
+                                           double om1, double o0, double op1, double op2)
 {
     // U_k = g_k - g_{k-s} at k = m-s, m, m+s, m+2s
     const double Um1 = gm1 - gm2, U0 = g0 - gm1, Up1 = gp1 - g0, Up2 = gp2 - gp1;
     // N_k = minmod(U_{k+s}, U_k): weight X on U_{k+s}, weight Y on U_k
     double xm1, ym1, x0, y0, xp1, yp1;
-    minmod_weights(U0, Um1, band, xm1, ym1);
-    minmod_weights(Up1, U0, band, x0, y0);
-    minmod_weights(Up2, Up1, band, xp1, yp1);
+    minmod_weights<kMode>(U0, Um1, xm1, ym1);
+    minmod_weights<kMode>(Up1, U0, x0, y0);
+    minmod_weights<kMode>(Up2, Up1, xp1, yp1);
     // N_bar_k = (l / 2) (o_{k+s} - o_k)  (from -l D_k and +l D_{k+s} / 2 ... see header)
     const double hl = 0.5 * l;
     const double Nbm1 = hl * (o0 - om1), Nb0 = hl * (op1 - o0), Nbp1 = hl * (op2 - op1);
@@ -204,12 +205,13 @@ __device__ __forceinline__ double flux_vjp(double l, double gm2, double gm1, dou
 
 // out_bar = c_prev * prev + VJP of one stage (see header) at stage input g for
 // cotangent ob; tau_acc[block] += sum over the block's cells of the tau term.
+template <int kMode>
 __global__ void __launch_bounds__(kAdjThreads) adjoint_stage_kernel(const double *__restrict__ g,
                                                                     const double *__restrict__ ob,
                                                                     const double *prev, double c_prev,
                                                                     double *out_bar, const StageArgs a,
                                                                     double gamma_h, double inv_tau,
-                                                                    double band, double *tau_acc)
+                                                                    double *tau_acc)
 {
     __shared__ double red[kAdjThreads];
     const int nx = a.nx, ny = a.ny;
@@ -262,7 +264,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_stage_kernel(const double
                 const double gm2 = gp[row + xs[2 - 2 * s]], gm1 = gp[row + xs[2 - s]];
                 const double gp1 = gp[row + xs[2 + s]], gp2 = gp[row + xs[2 + 2 * s]];
                 const double om1 = op[row + xs[2 - s]], op1 = op[row + xs[2 + s]], op2 = op[row + xs[2 + 2 * s]];
-                gb += flux_vjp(a.lx[grp], gm2, gm1, f[i], gp1, gp2, om1, o[i], op1, op2, band);
+                gb += flux_vjp<kMode>(a.lx[grp], gm2, gm1, f[i], gp1, gp2, om1, o[i], op1, op2);
             }
             if (diry(i) != 0 && ny > 1) {
                 const int s = diry(i);
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_stage_kernel(const double
                 const double gp1 = gp[(size_t)ys[2 + s] * nx + x], gp2 = gp[(size_t)ys[2 + 2 * s] * nx + x];
                 const double om1 = op[(size_t)ys[2 - s] * nx + x], op1 = op[(size_t)ys[2 + s] * nx + x];
                 const double op2 = op[(size_t)ys[2 + 2 * s] * nx + x];
-                gb += flux_vjp(a.ly[grp], gm2, gm1, f[i], gp1, gp2, om1, o[i], op1, op2, band);
+                gb += flux_vjp<kMode>(a.ly[grp], gm2, gm1, f[i], gp1, gp2, om1, o[i], op1, op2);
             }
             if (prev) gb = fma(c_prev, prev[i * P + c], gb);
             out_bar[i * P + c] = gb;
@@ -364,10 +366,18 @@ dim3 adjoint_grid(int nx, int ny) { return dim3((nx + kAdjThreads - 1) / kAdjThr
 
 cudaError_t launch_adjoint_stage(const double *g, const double *ob, const double *prev, double c_prev,
                                  double *out_bar, const StageArgs &a, double gamma_h, double inv_tau,
-                                 double band, double *tau_acc, cudaStream_t s)
+                                 int limiter, double *tau_acc, cudaStream_t s)
 {
-    adjoint_stage_kernel<<<adjoint_grid(a.nx, a.ny), kAdjThreads, 0, s>>>(g, ob, prev, c_prev, out_bar, a, gamma_h,
-                                                                          inv_tau, band, tau_acc);
+    const dim3 grid = adjoint_grid(a.nx, a.ny);
+    if (limiter == CDBM_ADJ_LIMITER_FROZEN_RATIO)
+        adjoint_stage_kernel<CDBM_ADJ_LIMITER_FROZEN_RATIO><<<grid, kAdjThreads, 0, s>>>(
+            g, ob, prev, c_prev, out_bar, a, gamma_h, inv_tau, tau_acc);
+    else if (limiter == CDBM_ADJ_LIMITER_FROZEN)
+        adjoint_stage_kernel<CDBM_ADJ_LIMITER_FROZEN><<<grid, kAdjThreads, 0, s>>>(
+            g, ob, prev, c_prev, out_bar, a, gamma_h, inv_tau, tau_acc);
+    else
+        adjoint_stage_kernel<CDBM_ADJ_LIMITER_EXACT><<<grid, kAdjThreads, 0, s>>>(
+            g, ob, prev, c_prev, out_bar, a, gamma_h, inv_tau, tau_acc);
     return cudaGetLastError();
 }
 

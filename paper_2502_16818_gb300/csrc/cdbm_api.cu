@@ -76,7 +76,7 @@ struct cdbm_ctx {
     int adj_steps, adj_every;     // steps recorded, checkpoint interval (0: none)
     long long step_count;         // steps taken since the state was set
     long long adj_end;            // step_count at the end of the recorded run
-    double adj_band;              // tie band of the limiter derivative (0: exact)
+    int adj_limiter;              // cdbm_adj_limiter of the adjoint (0: exact)
     std::vector<void *> ckpt;     // states at steps 0, k, 2k, ... of the recorded run
 
     cdbm_status err;
@@ -818,10 +818,10 @@ cdbm_status cdbm_adjoint_backward(cdbm_ctx *c, const double *fbar, double *grad_
         for (int j = len - 1; j >= 0 && !st; --j) {
             cudaError_t e = launch_stage(c->launch[0], seg[j], nullptr, G1, c->stage[0], c->flag, c->stream);
             if (e == cudaSuccess)   // stage 2: f^{n+1} = f^n/2 + f1/2 + dt/2 L(f1)
-                e = launch_adjoint_stage(G1, B, nullptr, 0.0, B1, c->stage[1], 0.5 * h, inv_tau, c->adj_band, acc,
+                e = launch_adjoint_stage(G1, B, nullptr, 0.0, B1, c->stage[1], 0.5 * h, inv_tau, c->adj_limiter, acc,
                                          c->stream);
             if (e == cudaSuccess)   // stage 1: f1 = f^n + dt L(f^n); plus the f^n/2 of stage 2
-                e = launch_adjoint_stage(seg[j], B1, B, 0.5, B, c->stage[0], h, inv_tau, c->adj_band, acc, c->stream);
+                e = launch_adjoint_stage(seg[j], B1, B, 0.5, B, c->stage[0], h, inv_tau, c->adj_limiter, acc, c->stream);
             st = cuda_check(c, e, "adjoint stage");
         }
     }
@@ -839,13 +839,13 @@ cdbm_status cdbm_adjoint_backward(cdbm_ctx *c, const double *fbar, double *grad_
     return st;
 }
 
-cdbm_status cdbm_adjoint_set_tie_band(cdbm_ctx *c, double band)
+cdbm_status cdbm_adjoint_set_limiter(cdbm_ctx *c, int mode)
 {
     if (!c) return CDBM_EINVAL;
     if (c->err) return c->err;
-    if (!(std::isfinite(band) && band >= 0.0 && band <= 1.0))
-        return set_err(c, CDBM_EINVAL, "cdbm_adjoint_set_tie_band: band must be in [0, 1]");
-    c->adj_band = band;
+    if (mode != CDBM_ADJ_LIMITER_EXACT && mode != CDBM_ADJ_LIMITER_FROZEN_RATIO && mode != CDBM_ADJ_LIMITER_FROZEN)
+        return set_err(c, CDBM_EINVAL, "cdbm_adjoint_set_limiter: unknown mode %d", mode);
+    c->adj_limiter = mode;
     return CDBM_OK;
 }
 

@@ -113,8 +113,16 @@ __device__ __forceinline__ void tube_stage(const TS *g, const TS *base, TS *out,
     }
 }
 
+// Register budget: 384 resident threads per SM for the double-precision equilibrium
+// (168 registers at 128 threads), 768 for the df64 one, whose float arithmetic fits
+// in 80 registers and gains from the extra warps as the single-grid stages do.
+constexpr int batch_min_blocks(int threads, bool df)
+{
+    return (df ? 768 : 384) / threads > 0 ? (df ? 768 : 384) / threads : 1;
+}
+
 template <typename TS, int kThreads, bool kDF>
-__global__ void __launch_bounds__(kThreads, (384 / kThreads > 0 ? 384 / kThreads : 1)) batch_kernel(TS *f, TS *f1, const TubeInfo *tubes,
+__global__ void __launch_bounds__(kThreads, batch_min_blocks(kThreads, kDF)) batch_kernel(TS *f, TS *f1, const TubeInfo *tubes,
                                                          const int *work, const int *work_off, int nsteps,
                                                          const BatchArgs a, unsigned *flag)
 {
@@ -621,15 +629,16 @@ cdbm_status cdbm_batch_autotune(cdbm_batch *b, int trial_steps, int *threads_out
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int cand_threads[3] = {64, 128, 256};
-    const int cand_bpsm[4] = {1, 2, 3, 4};
+    const int cand_bpsm[5] = {1, 2, 3, 4, 6};
+    const int max_threads = b->precision == CDBM_FP32_DF64 ? 1536 : 1024;
     float best = 1e30f;
     int bt = b->threads, bb = 3;
     cdbm_status st = CDBM_OK;
     if (bcuda(b, cudaMemcpyAsync(save, b->f, fb, cudaMemcpyDeviceToDevice, b->stream), "autotune backup"))
         st = b->err;
     for (int i = 0; i < 3 && st == CDBM_OK; ++i)
-        for (int j = 0; j < 4 && st == CDBM_OK; ++j) {
-            if (cand_threads[i] * cand_bpsm[j] > 1024) continue;
+        for (int j = 0; j < 5 && st == CDBM_OK; ++j) {
+            if (cand_threads[i] * cand_bpsm[j] > max_threads) continue;
             if ((st = set_tile(b, cand_threads[i], cand_bpsm[j])) != CDBM_OK) break;
             if ((st = launch_run(b, 1)) != CDBM_OK) break;        // warm-up
             cudaEventRecord(e0, b->stream);

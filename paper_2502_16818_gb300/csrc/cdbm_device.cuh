@@ -67,14 +67,15 @@ __device__ __forceinline__ double nnd(double u2, double u1, double c, double d1)
     return fma(0.5, t, a);
 }
 
-// Single-precision twins of minmod() and nnd() for the FP32-bulk state: same
-// expressions, with the limiter decided on the float's bit pattern.
+// Single-precision twins of minmod() and nnd() for the single-precision states.
+// minmod: the smaller magnitude with X's sign when the sign bits agree, else 0.  A
+// zero argument gives a zero result either way (min(|X|, |Y|) = 0), and equal
+// magnitudes with equal signs are the same value, so this is the Eq. (16) reading
+// of the double version; only the sign of an exact zero result may differ.
 __device__ __forceinline__ float minmod(float X, float Y)
 {
-    const int x = __float_as_int(X), y = __float_as_int(Y);
-    const unsigned ax = (unsigned)x & 0x7fffffffu, ay = (unsigned)y & 0x7fffffffu;
-    const bool keep = ((x ^ y) >= 0) & (ax != 0u) & (ay != 0u);
-    return __int_as_float(keep ? (ax <= ay ? x : y) : 0);
+    const float m = copysignf(fminf(fabsf(X), fabsf(Y)), X);
+    return (__float_as_int(X) ^ __float_as_int(Y)) >= 0 ? m : 0.0f;
 }
 
 __device__ __forceinline__ float nnd(float u2, float u1, float c, float d1)

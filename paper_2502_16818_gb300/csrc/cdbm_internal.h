@@ -147,10 +147,10 @@ cudaError_t launch_stage(const StageLaunch &L, const void *g, const void *base, 
 
 // ---- adjoint kernels (cdbm_adjoint.cu), double precision, periodic axes ----
 // out_bar = c_prev * prev + (stage VJP at g applied to ob); tau_acc[block] += tau term;
-// band: tie band of the limiter derivative (0: the exact branch derivative).
+// limiter: a cdbm_adj_limiter linearisation of minmod.
 cudaError_t launch_adjoint_stage(const double *g, const double *ob, const double *prev, double c_prev,
                                  double *out_bar, const StageArgs &a, double gamma_h, double inv_tau,
-                                 double band, double *tau_acc, cudaStream_t s);
+                                 int limiter, double *tau_acc, cudaStream_t s);
 dim3 adjoint_grid(int nx, int ny);
 cudaError_t launch_init_vjp(const FieldArgs &a, const double *f0, const double *fbar, double *rho_bar,
                             double *ux_bar, double *uy_bar, double *T_bar, cudaStream_t s);
