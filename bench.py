@@ -45,8 +45,7 @@ FP64_LANES_PER_CLK_PER_SM = 2       # 1.25 TFLOP/s nominal FP64 / (2 flops x 152
 
 # DRAM traffic of one stage launch (mean of the two stages) from one ncu capture of
 # the stage kernels; valid only while the kernel sources hash to TRAFFIC_SHA.
-# Captured at 1024^2 (134 MB per plane set, above L2) and scaled by 16 cells-fold; see
-# profiles/stage_kernel_tgv.md.
+# Captured at 1024^2 (134 MB per plane set, above L2) and scaled by 16 cells-fold.
 TRAFFIC_SHA = "38a1cf4a1024f862"
 TRAFFIC_BYTES_PER_LAUNCH = 5.098e9
 
@@ -77,6 +76,8 @@ def parse():
     p.add_argument("--ens-steps", type=int, default=200, help="timed steps of the tube ensemble")
     p.add_argument("--no-ensemble", action="store_true", help="skip the tube ensemble runs")
     p.add_argument("--no-configs", action="store_true", help="skip the per-configuration wall times")
+    p.add_argument("--cpu-configs", action="store_true",
+                   help="also time the oracle on each configuration (1 thread and all cores)")
     p.add_argument("--adj-steps", type=int, default=4000, help="steps of the adjoint run (0: skip it)")
     p.add_argument("--adj-every", type=int, default=200, help="checkpoint interval of the adjoint run")
     p.add_argument("--adj-n", type=int, default=1024, help="grid size of the adjoint run")
@@ -158,6 +159,37 @@ def cpu_baseline(w, side=2048, steps=8):
     return {"value": side * side * steps / dt, "unit": UNIT, "cores": m.threads, "kind": "oracle",
             "sample": "%dx%d block of the %d^2 Taylor-Green initial state, %d RK2 steps, "
                       "zero-gradient edges, %.1f s wall" % (side, side, w.nx, steps, dt)}
+
+
+def cpu_configs():
+    """The oracle (as it stands) on each configuration, on 1 thread and on all host
+    cores, each run bounded to about 10 s (2e6 cell-updates on one thread, 2e7 on
+    all cores): Sod, Lax, the sound wave 512^2 and a 1024^2 block of the 4096^2
+    vortex; cell-updates/s."""
+    import oracle
+    from paper_2502_16818_gb300 import workloads as W
+    tgv = W.taylor_green(n=4096, I=3.0)
+    block = [x[:1024, :1024] for x in (tgv.rho, tgv.ux, tgv.uy, tgv.T)]
+    runs = [("sod_500_I0", W.sod(nx=500, I=0.0), None, 10000), ("lax_2000_I0", W.lax(nx=2000, I=0.0), None, 10000)]
+    runs += [("sound_512_I%d" % I, W.sound(n=512, I=float(I)), None, 10) for I in (0, 1, 3)]
+    runs += [("taylor_green_4096_block1024", tgv, block, 4)]
+    res = {}
+    for name, w, fields, steps in runs:
+        row = {}
+        for threads in (1, os.cpu_count() or 1):
+            nx, ny = (1024, 1024) if fields else (w.nx, w.ny)
+            bc = (1, 1) if fields else (w.bc_x, w.bc_y)
+            m = oracle.Model(nx=nx, ny=ny, dx=w.dx, dy=w.dy, dt=w.dt, tau=w.tau, I=w.I, vg=w.vg, eg=w.eg,
+                             bc_x=bc[0], bc_y=bc[1], threads=threads)
+            f = oracle.init(m, *(fields or (w.rho, w.ux, w.uy, w.T)))
+            cap = 2e7 if threads > 1 else 2e6          # about 10 s of oracle work per run
+            n = max(1, min(steps, int(cap // (nx * ny))))
+            t0 = time.perf_counter()
+            oracle.step(m, f, n)
+            dt = time.perf_counter() - t0
+            row["threads_%d" % threads] = {"value": nx * ny * n / dt, "unit": UNIT, "steps": n, "s": dt}
+        res[name] = row
+    return res
 
 
 def run_reference(a, rank, world):
@@ -297,6 +329,8 @@ def run_cdbm(a, rank, world, local_rank):
             out["configs"] = configs(a, torch)
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, side=min(2048, w.nx))
+        if a.cpu_configs:
+            out["cpu_baseline"]["configs"] = cpu_configs()
     if rank == 0:
         print(json.dumps(out), flush=True)
 

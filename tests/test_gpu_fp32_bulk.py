@@ -179,3 +179,47 @@ def test_df64_as_accurate_as_double_equilibrium(shape):
     assert bool(torch.all(md <= 4.0 * mb + floor)), (md / (mb + floor)).max().item()
     l2b, l2d = torch.linalg.norm(e_bulk).item(), torch.linalg.norm(e_df).item()
     assert l2d <= 2.0 * l2b + floor, (l2d, l2b)
+
+
+def _patch(w, cy, cx, r):
+    """Sub-problem of radius r around (cy, cx) of a periodic workload's initial
+    fields, run by the oracle with zero-gradient edges that cannot reach the centre
+    within r/4 steps (stencil reach 2 per stage)."""
+    ys = np.arange(cy - r, cy + r + 1) % w.ny
+    xs = np.arange(cx - r, cx + r + 1) % w.nx
+    sub = [a[np.ix_(ys, xs)] for a in (w.rho, w.ux, w.uy, w.T)]
+    m = oracle.Model(nx=2 * r + 1, ny=2 * r + 1, dx=w.dx, dy=w.dy, dt=w.dt, tau=w.tau, I=w.I, vg=w.vg,
+                     eg=w.eg, bc_x=W.ZERO_GRADIENT, bc_y=W.ZERO_GRADIENT)
+    return m, sub
+
+
+def test_taylor_green_4096_sampled_single(prec):
+    """The full 4096^2 vortex in the launch configuration the benchmark times (the
+    row-marching kernel; 3 resident blocks per SM for FP32_BULK, 6 for FP32_DF64),
+    3 steps, sampled cells (random, block edges x = 127/128 and row-run edges at
+    multiples of 8, 16 and 32) against oracle patches.  After 103 steps the bench
+    measures per-field errors of ~3e-8 against FP64; the bar is 1e-6."""
+    from paper_2502_16818_gb300 import Solver
+    w = W.taylor_green(n=4096, I=3.0)
+    steps = 3
+    s = Solver.from_workload(w, precision=prec)
+    s.init(w.rho, w.ux, w.uy, w.T)
+    s.step(steps)
+    s.sync()
+    got = [t.cpu().numpy() for t in s.macros()]
+    s.close()
+    rng = np.random.default_rng(17)
+    pts = [(int(rng.integers(w.ny)), int(rng.integers(w.nx))) for _ in range(16)]
+    pts += [(r + d, 128 * j + e) for r in (8, 16, 32, 320, 1024, 4064) for d in (-1, 0)
+            for j in (1, 17) for e in (-1, 0)]
+    pts += [(0, 0), (w.ny - 1, w.nx - 1)]
+    cs = math.sqrt(W.gamma_of(w.I) * float(np.mean(got[3])))
+    us = max(np.abs(got[1]).max(), np.abs(got[2]).max(), cs)
+    scale = [np.abs(got[0]).max(), us, us, np.abs(got[3]).max()]
+    r = 4 * steps + 2
+    for cy, cx in pts:
+        m, sub = _patch(w, cy, cx, r)
+        ref = oracle.macros(m, oracle.step(m, oracle.init(m, *sub), steps))
+        for k in range(4):
+            e = abs(got[k][cy, cx] - ref[k][r, r]) / scale[k]
+            assert e <= 1e-6, (k, cy, cx, e)
