@@ -133,10 +133,18 @@ cdbm_status cdbm_init(cdbm_ctx *ctx, const double *rho, const double *ux, const 
 /*
  * cdbm_step -- advances the state by nsteps >= 0 time steps of Eq. (1): per step two
  * fused Runge-Kutta stage kernels (rho, u, T -> f_eq -> BGK + NND transport of all
- * 16 velocities -> stage update).  Launches are replayed from a CUDA graph.
- * Asynchronous; a non-physical state is reported by the next cdbm_sync.
+ * 16 velocities -> stage update).  Launches are replayed from a CUDA graph.  A 1-D
+ * grid (ny = 1) small enough for one thread-block cluster (at most 16 x 64 cells for
+ * CDBM_FP64, 16 x 256 for the single-precision states) instead runs all nsteps in
+ * one persistent launch with its state in the cluster's shared memory; the results
+ * are the same bit for bit.  Asynchronous; a non-physical state is reported by the
+ * next cdbm_sync.
  */
 cdbm_status cdbm_step(cdbm_ctx *ctx, int nsteps);
+
+/* Enables (default) or disables the persistent cluster path of cdbm_step for small
+ * 1-D grids; disabled, those grids step with one launch per stage like any other. */
+cdbm_status cdbm_set_small_grid_path(cdbm_ctx *ctx, int enable);
 
 /*
  * cdbm_macros -- writes rho, u_x, u_y, T of the current state ([ny][nx] each,

@@ -25,8 +25,8 @@ CDBM_ADJ_LIMITER_EXACT, CDBM_ADJ_LIMITER_FROZEN_RATIO, CDBM_ADJ_LIMITER_FROZEN =
 CDBM_RK2_TVD, CDBM_RK2_MIDPOINT = 0, 1
 
 #: every entry point declared in include/cdbm.h
-EXPORTS = ("cdbm_create", "cdbm_set_rk", "cdbm_init", "cdbm_step", "cdbm_macros", "cdbm_tne",
-           "cdbm_conserved_sums", "cdbm_get_state", "cdbm_set_state", "cdbm_state_ptr", "cdbm_time",
+EXPORTS = ("cdbm_create", "cdbm_set_rk", "cdbm_init", "cdbm_step", "cdbm_set_small_grid_path", "cdbm_macros",
+           "cdbm_tne", "cdbm_conserved_sums", "cdbm_get_state", "cdbm_set_state", "cdbm_state_ptr", "cdbm_time",
            "cdbm_sync", "cdbm_last_error", "cdbm_destroy", "cdbm_step_noalloc",
            "cdbm_batch_create", "cdbm_batch_init", "cdbm_batch_step", "cdbm_batch_autotune",
            "cdbm_batch_set_tile", "cdbm_batch_macros", "cdbm_batch_info", "cdbm_batch_sync",
@@ -84,6 +84,7 @@ def load(path: str | None = None):
         "cdbm_set_rk": ([ctx, ctypes.c_int], ctypes.c_int),
         "cdbm_init": ([ctx, _vp, _vp, _vp, _vp], ctypes.c_int),
         "cdbm_step": ([ctx, ctypes.c_int], ctypes.c_int),
+        "cdbm_set_small_grid_path": ([ctx, ctypes.c_int], ctypes.c_int),
         "cdbm_macros": ([ctx, _vp, _vp, _vp, _vp], ctypes.c_int),
         "cdbm_tne": ([ctx, _vp], ctypes.c_int),
         "cdbm_conserved_sums": ([ctx, _dp], ctypes.c_int),
@@ -154,6 +155,11 @@ def cdbm_init(ctx, rho, ux, uy, T):
 def cdbm_step(ctx, nsteps):
     lib = load()
     _check(lib, ctx, lib.cdbm_step(ctx, int(nsteps)))
+
+
+def cdbm_set_small_grid_path(ctx, enable):
+    lib = load()
+    _check(lib, ctx, lib.cdbm_set_small_grid_path(ctx, int(bool(enable))))
 
 
 def cdbm_macros(ctx, rho, ux, uy, T):

@@ -18,6 +18,7 @@ namespace {
 thread_local char g_create_error[kThreadErrorBytes] = "no error";
 
 constexpr int kGraphSteps = 32;       // time steps per replayed CUDA graph
+constexpr int kSmallSteps = 65536;    // time steps per launch of the small-grid cluster kernel
 constexpr double kMaxCond = 1e12;     // condition limit of the moment blocks
 
 struct RkStage {
@@ -71,6 +72,8 @@ struct cdbm_ctx {
     FieldArgs fields;
 
     cudaGraphExec_t graph;
+    Small1D small;                // persistent cluster path for small 1-D grids
+    bool small_enabled;
 
     // adjoint record of the last cdbm_adjoint_forward
     int adj_steps, adj_every;     // steps recorded, checkpoint interval (0: none)
@@ -338,6 +341,7 @@ void build_stages(cdbm_ctx *c)
         fill_df_consts(a);
         c->launch[s] = stage_launch_config(a, r.with_base, c->sm_count, c->precision);
     }
+    c->small = small1d_config(c->stage[0], c->precision);
 }
 
 cdbm_status enqueue_step(cdbm_ctx *c)
@@ -444,6 +448,7 @@ cdbm_status cdbm_create(const cdbm_grid *grid, const cdbm_vset *vset, double I, 
     c->dt = dt;
     c->precision = precision;
     c->rk = CDBM_RK2_TVD;
+    c->small_enabled = true;
     c->stream = (cudaStream_t)cuda_stream;
     c->user_alloc = allocator && allocator->alloc && allocator->free;
     if (c->user_alloc) c->alloc = *allocator;
@@ -569,6 +574,16 @@ cdbm_status cdbm_step(cdbm_ctx *c, int nsteps)
     if (nsteps < 0) return set_err(c, CDBM_EINVAL, "cdbm_step: nsteps < 0");
     if (!c->state_set) return set_err(c, CDBM_EINVAL, "cdbm_step: state not initialised");
     int left = nsteps;
+    if (c->small.ok && c->small_enabled) {
+        // whole run in persistent launches of at most kSmallSteps steps
+        while (left > 0) {
+            const int n = left < kSmallSteps ? left : kSmallSteps;
+            if (cuda_check(c, launch_small1d(c->small, c->f, n, c->stage[0], c->stage[1], c->flag, c->stream),
+                           "small-grid launch"))
+                return c->err;
+            left -= n;
+        }
+    }
     if (left >= kGraphSteps && !c->graph && build_graph(c)) return c->err;
     while (left >= kGraphSteps) {
         if (cuda_check(c, cudaGraphLaunch(c->graph, c->stream), "graph launch")) return c->err;
@@ -578,6 +593,14 @@ cdbm_status cdbm_step(cdbm_ctx *c, int nsteps)
         if (enqueue_step(c)) return c->err;
     c->t += nsteps * c->dt;
     c->step_count += nsteps;
+    return CDBM_OK;
+}
+
+cdbm_status cdbm_set_small_grid_path(cdbm_ctx *c, int enable)
+{
+    if (!c) return CDBM_EINVAL;
+    if (c->err) return c->err;
+    c->small_enabled = enable != 0;
     return CDBM_OK;
 }
 

@@ -145,6 +145,18 @@ StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count
 cudaError_t launch_stage(const StageLaunch &L, const void *g, const void *base, void *out,
                          const StageArgs &a, unsigned *flag, cudaStream_t s);
 
+// Persistent cluster kernel for small 1-D grids (cdbm_small1d.cu): the whole state in
+// the shared memory of one thread-block cluster, nsteps steps in one launch.
+struct Small1D {
+    bool ok;                      // the grid qualifies and the cluster fits on the device
+    void *func;
+    int cluster, chunk, threads;  // CTAs, cells per CTA, threads per CTA
+    size_t smem;                  // dynamic shared memory per CTA
+};
+Small1D small1d_config(const StageArgs &a, int prec);
+cudaError_t launch_small1d(const Small1D &L, void *f, int nsteps, const StageArgs &a0, const StageArgs &a1,
+                           unsigned *flag, cudaStream_t s);
+
 // ---- adjoint kernels (cdbm_adjoint.cu), double precision, periodic axes ----
 // out_bar = c_prev * prev + (stage VJP at g applied to ob); tau_acc[block] += tau term;
 // limiter: a cdbm_adj_limiter linearisation of minmod.

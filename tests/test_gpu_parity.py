@@ -425,3 +425,32 @@ def test_macros_roundtrip_extreme_density():
     # u = j / rho with |j| summing terms of size rho * O(1): absolute rounding ~1e-15
     np.testing.assert_allclose(got[1], w.ux, rtol=1e-13, atol=1e-14)
     np.testing.assert_allclose(got[3], w.T, rtol=1e-13)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("rk", [0, 1])
+@pytest.mark.parametrize("bc", [W.ZERO_GRADIENT, W.PERIODIC])
+def test_small_grid_cluster_path_matches_stage_launches(prec, rk, bc):
+    """1-D grids small enough for one thread-block cluster run a whole cdbm_step in
+    one persistent launch (state in shared memory, halos over distributed shared
+    memory).  The same run with that path disabled (one launch per stage) must give
+    the same state bit for bit: 1 cell, partial last CTA, one cell per CTA, full
+    clusters of 16 CTAs, and step counts that are not multiples of the graph length."""
+    from paper_2502_16818_gb300 import Solver, cdbm
+    limit = 16 * (64 if prec == 0 else 256)
+    for nx in (1, 5, 16, 37, 500, limit):
+        w = W.random_blocks(nx, 1, seed=nx + 7, bc=(bc, W.PERIODIC))
+        w.dx = 1.0 / max(nx, 8)
+        w.dt = 0.2 * w.dx / 2.2
+        w.tau = 2 * w.dt
+        states = []
+        for enable in (1, 0):
+            s = Solver.from_workload(w, precision=prec, rk=rk)
+            cdbm.cdbm_set_small_grid_path(s.ctx, enable)
+            s.init(w.rho, w.ux, w.uy, w.T)
+            s.step(37)
+            s.step(5)
+            s.sync()
+            states.append(s.state().cpu().numpy())
+            s.close()
+        assert np.array_equal(states[0], states[1]), (nx, prec, rk, bc)
