@@ -34,20 +34,22 @@ METRIC = "cell-updates/s and HBM GB/s vs FP64 plain on same GB300 at stated L2 e
 UNIT = "cell-updates/s"
 
 # FP64 work of the fused (row-marching) stage kernels per cell.  Instructions: ncu
-# sm__inst_executed_pipe_fp64 per warp of 32 cells (stage 1: 272, stage 2: 288).
-# Flops, counted from the kernel source with an FMA as two flops: stage 1: 400,
-# stage 2: 432.  Bytes per cell-step: stage 1 reads f^n and writes f1 (128 + 128 B);
-# stage 2 reads f1 and f^n and writes f^n+1 (384 B).
-FP64_INSTR_PER_CELL_STEP = 560
-FP64_FLOPS_PER_CELL_STEP = 832
+# sm__inst_executed_pipe_fp64 per warp of 32 cells (stage 1: 254, stage 2: 270).
+# Flops, counted from the kernel source with an FMA as two flops: stage 1: 376,
+# stage 2: 408 (each x difference computed once per cell and shared through the row
+# buffer; the halo recomputation of the block-edge threads is not counted).  Bytes
+# per cell-step: stage 1 reads f^n and writes f1 (128 + 128 B); stage 2 reads f1 and
+# f^n and writes f^n+1 (384 B).
+FP64_INSTR_PER_CELL_STEP = 524
+FP64_FLOPS_PER_CELL_STEP = 784
 BYTES_PER_CELL_STEP = 640
 FP64_LANES_PER_CLK_PER_SM = 2       # 1.25 TFLOP/s nominal FP64 / (2 flops x 152 SMs x 2.07 GHz)
 
 # DRAM traffic of one stage launch (mean of the two stages) from one ncu capture of
 # the stage kernels; valid only while the kernel sources hash to TRAFFIC_SHA.
 # Captured at 1024^2 (134 MB per plane set, above L2) and scaled by 16 cells-fold.
-TRAFFIC_SHA = "38a1cf4a1024f862"
-TRAFFIC_BYTES_PER_LAUNCH = 5.098e9
+TRAFFIC_SHA = "f8c6c091a8a26146"
+TRAFFIC_BYTES_PER_LAUNCH = 5.105e9
 
 
 STAGE_SOURCES = ("cdbm_device.cuh", "cdbm_kernels.cu", "cdbm_internal.h")

@@ -134,22 +134,36 @@ template <typename TS, bool kBase, bool kDF>
 __global__ void __launch_bounds__(kStageThreads, stage_min_blocks(kDF))
     stage_march_kernel(const TS *__restrict__ g, const TS *base, TS *out, const StageArgs a, unsigned *flag)
 {
+    // In double precision the x differences are shared as well: each thread computes
+    // U_x = f_x - f_{x-s} of its cell once per velocity and reads U_{x+s}, U_{x-s} of
+    // its neighbours from a row buffer (two block barriers per row; the edge threads
+    // add the halo values), so an x-term costs 4 FP64 instructions plus a share of the
+    // halo instead of 6.  The operands and operations are those of nnd(), so the
+    // result is the same bit for bit.  In single precision the FP32 arithmetic is not
+    // the scarce unit and the plain three-load form is kept.
+    constexpr bool kShareX = !kSingle<TS>;
+    constexpr int kNXV = 12;                          // velocities with an x component
     __shared__ TS carry_u[kNY][kStageThreads];
     __shared__ TS carry_n[kNY][kStageThreads];
+    __shared__ TS row_u[kShareX ? kNXV : 1][kShareX ? kStageThreads + 2 : 1];
     const int nx = a.nx, ny = a.ny;
     const int tid = threadIdx.x;
     const int x = blockIdx.x * blockDim.x + tid;
-    if (x >= nx) return;
+    const bool active = x < nx;
+    if (!kShareX && !active) return;
     const int R = (ny + gridDim.y - 1) / gridDim.y;
     const int y0 = blockIdx.y * R;
     const int y1 = y0 + R < ny ? y0 + R : ny;
-    if (y0 >= y1) return;
+    if (y0 >= y1) return;                             // the same for the whole block
+    const int last = (nx - (int)(blockIdx.x * blockDim.x) < (int)blockDim.x
+                          ? nx - (int)(blockIdx.x * blockDim.x) : (int)blockDim.x) - 1;   // last active thread
     const size_t P = (size_t)nx * ny;
-    const int xm2 = neighbour(x - 2, nx, a.bc_x), xm1 = neighbour(x - 1, nx, a.bc_x);
-    const int xp1 = neighbour(x + 1, nx, a.bc_x), xp2 = neighbour(x + 2, nx, a.bc_x);
+    const int xc = active ? x : nx - 1;               // inactive threads only pass the barriers
+    const int xm2 = neighbour(xc - 2, nx, a.bc_x), xm1 = neighbour(xc - 1, nx, a.bc_x);
+    const int xp1 = neighbour(xc + 1, nx, a.bc_x), xp2 = neighbour(xc + 2, nx, a.bc_x);
 
     // prologue: U_{y0} and N_{y0 - 1} for s = +1, N_{y0} for s = -1
-    {
+    if (active) {
         const size_t r0 = (size_t)y0 * nx + x;
         const size_t rm1 = (size_t)neighbour(y0 - 1, ny, a.bc_y) * nx + x;
         const size_t rm2 = (size_t)neighbour(y0 - 2, ny, a.bc_y) * nx + x;
@@ -175,52 +189,101 @@ __global__ void __launch_bounds__(kStageThreads, stage_min_blocks(kDF))
 
     for (int y = y0; y < y1; ++y) {
         const size_t row = (size_t)y * nx;
-        const size_t c = row + x;
-        const size_t rp1 = (size_t)neighbour(y + 1, ny, a.bc_y) * nx + x;
-        const size_t rp2 = (size_t)neighbour(y + 2, ny, a.bc_y) * nx + x;
-        TS fs[kNV];
+        const size_t c = row + xc;
+        TS fs[kNV], o[kNV];
+        if (active) {
 #pragma unroll
-        for (int i = 0; i < kNV; ++i) fs[i] = __ldg(g + i * P + c);
-        TS heq[kNV];
-        stage_equilibrium<TS, kDF>(a, fs, heq, flag);
-
-        TS o[kNV];
+            for (int i = 0; i < kNV; ++i) fs[i] = __ldg(g + i * P + c);
+            TS heq[kNV];
+            stage_equilibrium<TS, kDF>(a, fs, heq, flag);
+            int k = 0;
 #pragma unroll
-        for (int i = 0; i < kNV; ++i) {
-            o[i] = fma_t(a_self_of<TS>(a), fs[i], heq[i]);
-            if (kBase) o[i] = fma_t(a_base_of<TS>(a), base[i * P + c], o[i]);
-            if (dirx(i) != 0) {
-                const TS *gp = g + i * P + row;
-                const TS u2 = __ldg(gp + (dirx(i) > 0 ? xm2 : xp2));
-                const TS u1 = __ldg(gp + (dirx(i) > 0 ? xm1 : xp1));
-                const TS d1 = __ldg(gp + (dirx(i) > 0 ? xp1 : xm1));
-                o[i] = fma_t(-lx_of<TS>(a, i >> 2), nnd(u2, u1, fs[i], d1), o[i]);
+            for (int i = 0; i < kNV; ++i) {
+                o[i] = fma_t(a_self_of<TS>(a), fs[i], heq[i]);
+                if (kBase) o[i] = fma_t(a_base_of<TS>(a), base[i * P + c], o[i]);
+                if (dirx(i) != 0) {
+                    const TS *gp = g + i * P + row;
+                    const TS u1 = __ldg(gp + (dirx(i) > 0 ? xm1 : xp1));
+                    if constexpr (kShareX) {
+                        row_u[k][tid + 1] = fs[i] - u1;            // U at x: the upwind-ordered a of nnd()
+                    } else {
+                        const TS u2 = __ldg(gp + (dirx(i) > 0 ? xm2 : xp2));
+                        const TS d1 = __ldg(gp + (dirx(i) > 0 ? xp1 : xm1));
+                        o[i] = fma_t(-lx_of<TS>(a, i >> 2), nnd(u2, u1, fs[i], d1), o[i]);
+                    }
+                    ++k;
+                }
             }
         }
+        if constexpr (kShareX) {
+            // Halo of the row buffer: U_{x-1} left of the block and U_{x+1} right of it (the
+            // e or b of nnd() of the edge cells).  One branch taken by the edge threads only,
+            // so the other warps do not issue these instructions.
+            if (active && tid == 0) {
+                int k = 0;
 #pragma unroll
-        for (int k = 0; k < kNY; ++k) {
-            const int i = yvel(k);
-            const TS *gp = g + i * P;
-            const TS u = carry_u[k][tid];
-            const TS n = carry_n[k][tid];
-            TS t;
-            if (diry(i) > 0) {
-                const TS un = __ldg(gp + rp1) - fs[i];                  // U_{y+1}
-                const TS nn = minmod(un, u);                            // N_y
-                t = nn - n;                                             // N_y - N_{y-1}
-                carry_u[k][tid] = un;
-                carry_n[k][tid] = nn;
-            } else {
-                const TS un = __ldg(gp + rp1) - __ldg(gp + rp2);        // U_{y+1}
-                const TS nn = minmod(u, un);                            // N_{y+1}
-                t = n - nn;                                             // N_y - N_{y+1}
-                carry_u[k][tid] = un;
-                carry_n[k][tid] = nn;
+                for (int i = 0; i < kNV; ++i) {
+                    if (dirx(i) == 0) continue;
+                    const TS *gp = g + i * P + row;
+                    row_u[k][0] = dirx(i) > 0 ? __ldg(gp + xm1) - __ldg(gp + xm2) : __ldg(gp + xm1) - fs[i];
+                    ++k;
+                }
             }
-            o[i] = fma_t(-ly_of<TS>(a, i >> 2), fma_t((TS)0.5, t, u), o[i]);
-        }
+            if (active && tid == last) {
+                int k = 0;
 #pragma unroll
-        for (int i = 0; i < kNV; ++i) out[i * P + c] = o[i];
+                for (int i = 0; i < kNV; ++i) {
+                    if (dirx(i) == 0) continue;
+                    const TS *gp = g + i * P + row;
+                    row_u[k][last + 2] = dirx(i) > 0 ? __ldg(gp + xp1) - fs[i] : __ldg(gp + xp1) - __ldg(gp + xp2);
+                    ++k;
+                }
+            }
+            __syncthreads();
+            if (active) {
+                int k = 0;
+#pragma unroll
+                for (int i = 0; i < kNV; ++i) {
+                    if (dirx(i) == 0) continue;
+                    const int s = dirx(i);
+                    const TS av = row_u[k][tid + 1];              // c - u1
+                    const TS bv = row_u[k][tid + 1 + s];          // d1 - c
+                    const TS ev = row_u[k][tid + 1 - s];          // u1 - u2
+                    const TS t = minmod(bv, av) - minmod(av, ev);
+                    o[i] = fma_t(-lx_of<TS>(a, i >> 2), fma_t((TS)0.5, t, av), o[i]);
+                    ++k;
+                }
+            }
+            __syncthreads();
+        }
+        if (active) {
+            const size_t rp1 = (size_t)neighbour(y + 1, ny, a.bc_y) * nx + x;
+            const size_t rp2 = (size_t)neighbour(y + 2, ny, a.bc_y) * nx + x;
+#pragma unroll
+            for (int k = 0; k < kNY; ++k) {
+                const int i = yvel(k);
+                const TS *gp = g + i * P;
+                const TS u = carry_u[k][tid];
+                const TS n = carry_n[k][tid];
+                TS t;
+                if (diry(i) > 0) {
+                    const TS un = __ldg(gp + rp1) - fs[i];                  // U_{y+1}
+                    const TS nn = minmod(un, u);                            // N_y
+                    t = nn - n;                                             // N_y - N_{y-1}
+                    carry_u[k][tid] = un;
+                    carry_n[k][tid] = nn;
+                } else {
+                    const TS un = __ldg(gp + rp1) - __ldg(gp + rp2);        // U_{y+1}
+                    const TS nn = minmod(u, un);                            // N_{y+1}
+                    t = n - nn;                                             // N_y - N_{y+1}
+                    carry_u[k][tid] = un;
+                    carry_n[k][tid] = nn;
+                }
+                o[i] = fma_t(-ly_of<TS>(a, i >> 2), fma_t((TS)0.5, t, u), o[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < kNV; ++i) out[i * P + c] = o[i];
+        }
     }
 }
 
