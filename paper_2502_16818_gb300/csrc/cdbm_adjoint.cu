@@ -68,16 +68,13 @@ struct MomBar {
 // (d out / d m)^T ob for out = equilibrium(B, m, ...) (scaled as B is), m = (rho, jx,
 // jy, E): reverse of the forward sequence in equilibrium() and primitives(), step by
 // step.  With r = 1/rho, u = j r, ru2 = j.u, P = (E - ru2)/K, T = P r.
-__device__ __forceinline__ MomBar equilibrium_vjp(const EqBlocks &B, const ModelConsts &m, double rho,
-                                                  double jx, double jy, double E, const double ob[kNV])
+// The forward values r = 1/rho, u, j_y u_y, rho u^2, P and T come from the caller
+// (primitives() of the forward stage, the same refined reciprocal).
+__device__ __forceinline__ MomBar equilibrium_vjp(const EqBlocks &B, const ModelConsts &m, double jx, double jy,
+                                                  double r, double ux, double uy, double jyuy, double ru2,
+                                                  double P, double T, const double ob[kNV])
 {
     // forward values
-    const double r = 1.0 / rho;
-    const double ux = jx * r, uy = jy * r;
-    const double jyuy = jy * uy;
-    const double ru2 = fma(jx, ux, jyuy);
-    const double P = (E - ru2) * m.invK;
-    const double T = P * r;
     const double ux2 = ux * ux, uy2 = uy * uy, u2 = ux2 + uy2;
     const double Y = fma(m.Kp6, ru2, m.twoKp2 * P);
     const double W4 = fma(m.Kp4, T, u2);
@@ -228,19 +225,16 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_stage_kernel(const double
             f[i] = g[i * P + c];
             o[i] = ob[i * P + c];
         }
-        const Cons q = conserved(f, a.m);
-        const double r = 1.0 / q.rho;
-        const double ux = q.jx * r, uy = q.jy * r;
-        const double jyuy = q.jy * uy;
-        const double ru2 = fma(q.jx, ux, jyuy);
-        const double p = (q.E - ru2) * a.m.invK;
-        const double T = p * r;
+        unsigned nonphys = 0;                              // the forward stage already reported it
+        const Prim pr = primitives<false>(f, a.m, 0.0, 0.0, &nonphys);
+        const Cons &q = pr.q;
         double heq[kNV];
-        equilibrium(a.eq, a.m, q.rho, q.E, q.jx, q.jy, ux, uy, ru2, jyuy, p, T, heq);
+        equilibrium(a.eq, a.m, q.rho, q.E, q.jx, q.jy, pr.ux, pr.uy, pr.ru2, pr.jyuy, pr.p, pr.T, heq);
 #pragma unroll
         for (int i = 0; i < kNV; ++i) tau_part = fma(o[i], fma(gamma_h, f[i], -heq[i]), tau_part);
         tau_part *= inv_tau;
-        const MomBar w = equilibrium_vjp(a.eq, a.m, q.rho, q.jx, q.jy, q.E, o);
+        const MomBar w = equilibrium_vjp(a.eq, a.m, q.jx, q.jy, pr.r, pr.ux, pr.uy, pr.jyuy, pr.ru2, pr.p, pr.T,
+                                         o);
 
         int xs[5];
 #pragma unroll
@@ -302,8 +296,11 @@ __global__ void __launch_bounds__(128) init_vjp_kernel(const FieldArgs a, const 
             f[i] = f0[i * P + c];
             o[i] = fbar[i * P + c];
         }
-        const Cons q = conserved(f, a.m);
-        const MomBar w = equilibrium_vjp(a.eq, a.m, q.rho, q.jx, q.jy, q.E, o);
+        unsigned nonphys = 0;
+        const Prim pr = primitives<false>(f, a.m, 0.0, 0.0, &nonphys);
+        const Cons &q = pr.q;
+        const MomBar w = equilibrium_vjp(a.eq, a.m, q.jx, q.jy, pr.r, pr.ux, pr.uy, pr.jyuy, pr.ru2, pr.p, pr.T,
+                                         o);
         // m = (rho, rho u_x, rho u_y, rho (u^2 + K T)) of the fields
         const double u = q.jx / q.rho, v = q.jy / q.rho;
         const double T = (q.E - fma(q.jx, u, q.jy * v)) / (a.m.K * q.rho);

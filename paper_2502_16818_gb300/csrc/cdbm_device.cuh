@@ -195,6 +195,7 @@ __device__ __forceinline__ float fma_t(float x, float y, float z) { return fmaf(
 // g = f - F and the reference moments rhoF, EF are added.
 struct Prim {
     Cons q;
+    double r;                    // 1 / rho
     double ux, uy, jyuy, ru2, p, T;
 };
 
@@ -209,6 +210,7 @@ __device__ __forceinline__ Prim primitives(const double f[kNV], const ModelConst
         s.q.E += EF;
     }
     const double r = rcp64(s.q.rho);
+    s.r = r;
     s.ux = s.q.jx * r;
     s.uy = s.q.jy * r;
     s.jyuy = s.q.jy * s.uy;
