@@ -48,7 +48,7 @@ FP64_LANES_PER_CLK_PER_SM = 2       # 1.25 TFLOP/s nominal FP64 / (2 flops x 152
 # DRAM traffic of one stage launch (mean of the two stages) from one ncu capture of
 # the stage kernels; valid only while the kernel sources hash to TRAFFIC_SHA.
 # Captured at 1024^2 (134 MB per plane set, above L2) and scaled by 16 cells-fold.
-TRAFFIC_SHA = "f8c6c091a8a26146"
+TRAFFIC_SHA = "58f7dbe1b5a75647"
 TRAFFIC_BYTES_PER_LAUNCH = 5.105e9
 
 

@@ -176,28 +176,39 @@ __device__ __forceinline__ MomBar equilibrium_vjp(const EqBlocks &B, const Model
 // cell m from the terms -l D_j of the cells j whose stencil contains m, given g at
 // m-2s .. m+2s (gm2 .. gp2 in upwind order: gm2 = g_{m-2s}, ..., gp2 = g_{m+2s}) and
 // the cotangent o at m-s .. m+2s.
+//
+// With U_k = g_k - g_{k-s}, N_k = minmod(U_{k+s}, U_k) linearised as
+// dN_k = w_X(k) dU_{k+s} + w_Y(k) dU_k, and d_k = o_{k+s} - o_k, the transpose of
+// -l D_j = -l (U_j + (N_j - N_{j-s}) / 2) collected at g_m is
+//   g_bar_m = (l / 2) [ (2 + w_Y(m) - w_X(m)) d_m + w_X(m-s) d_{m-s} - w_Y(m+s) d_{m+s} ],
+// written with the halved coefficients so that one product by l remains.  In the
+// frozen mode all weights vanish and it is l d_m.
 template <int kMode>
 __device__ __forceinline__ double flux_vjp(double l, double gm2, double gm1, double g0, double gp1, double gp2,
                                            double om1, double o0, double op1, double op2)
 {
-    // U_k = g_k - g_{k-s} at k = m-s, m, m+s, m+2s
+    const double d0 = op1 - o0;
+    if (kMode == CDBM_ADJ_LIMITER_FROZEN) return l * d0;
+    const double dm1 = o0 - om1, dp1 = op2 - op1;
+    // U_k at k = m-s, m, m+s, m+2s
     const double Um1 = gm1 - gm2, U0 = g0 - gm1, Up1 = gp1 - g0, Up2 = gp2 - gp1;
-    // N_k = minmod(U_{k+s}, U_k): weight X on U_{k+s}, weight Y on U_k
-    double xm1, ym1, x0, y0, xp1, yp1;
-    minmod_weights<kMode>(U0, Um1, xm1, ym1);
-    minmod_weights<kMode>(Up1, U0, x0, y0);
-    minmod_weights<kMode>(Up2, Up1, xp1, yp1);
-    // N_bar_k = (l / 2) (o_{k+s} - o_k)  (from -l D_k and +l D_{k+s} / 2 ... see header)
-    const double hl = 0.5 * l;
-    const double Nbm1 = hl * (o0 - om1), Nb0 = hl * (op1 - o0), Nbp1 = hl * (op2 - op1);
-    // U_bar_k = -l o_k + w_X(N_{k-s}) N_bar_{k-s} + w_Y(N_k) N_bar_k
-    double Ub0 = -l * o0, Ubp1 = -l * op1;
-    Ub0 = fma(xm1, Nbm1, Ub0);
-    Ub0 = fma(y0, Nb0, Ub0);
-    Ubp1 = fma(x0, Nb0, Ubp1);
-    Ubp1 = fma(yp1, Nbp1, Ubp1);
-    // U_k = g_k - g_{k-s}: g_bar_m = U_bar_m - U_bar_{m+s}
-    return Ub0 - Ubp1;
+    double acc;
+    if (kMode == CDBM_ADJ_LIMITER_EXACT) {
+        // branch of N_{m-s}, N_m, N_{m+s}: 1 picks X = U_{k+s}, 2 picks Y = U_k, 0 is zero
+        const int bm1 = minmod_branch(U0, Um1), b0 = minmod_branch(Up1, U0), bp1 = minmod_branch(Up2, Up1);
+        acc = (b0 == 1 ? 0.5 : (b0 == 2 ? 1.5 : 1.0)) * d0;
+        acc = fma(bm1 == 1 ? 0.5 : 0.0, dm1, acc);
+        acc = fma(bp1 == 2 ? -0.5 : 0.0, dp1, acc);
+    } else {
+        double xm1, ym1, x0, y0, xp1, yp1;
+        minmod_weights<kMode>(U0, Um1, xm1, ym1);
+        minmod_weights<kMode>(Up1, U0, x0, y0);
+        minmod_weights<kMode>(Up2, Up1, xp1, yp1);
+        acc = fma(0.5, y0 - x0, 1.0) * d0;
+        acc = fma(0.5 * xm1, dm1, acc);
+        acc = fma(-0.5 * yp1, dp1, acc);
+    }
+    return l * acc;
 }
 
 // out_bar = c_prev * prev + VJP of one stage (see header) at stage input g for

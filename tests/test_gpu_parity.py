@@ -261,8 +261,8 @@ def _patch(w, cy, cx, r):
     return m, sub, py, px
 
 
-def _sampled_check(w, steps, nsamp, seed, edges=False):
-    s = solver(w)
+def _sampled_check(w, steps, nsamp, seed, edges=False, rk=0):
+    s = solver(w, rk=rk)
     s.init(w.rho, w.ux, w.uy, w.T)
     s.step(steps)
     s.sync()
@@ -282,6 +282,7 @@ def _sampled_check(w, steps, nsamp, seed, edges=False):
     scale = [np.abs(got[0]).max(), us, us, np.abs(got[3]).max()]
     for (cy, cx) in pts:
         m, sub, py, px = _patch(w, cy, cx, r)
+        m.rk = rk
         fo = oracle.step(m, oracle.init(m, *sub), steps)
         ref = oracle.macros(m, fo)
         for k, name in enumerate(FIELDS):
@@ -303,16 +304,18 @@ def test_taylor_green_4096_sampled():
     _sampled_check(W.taylor_green(n=4096, I=3.0), 3, 24, seed=4)
 
 
+@pytest.mark.parametrize("rk", [0, 1], ids=["tvd", "midpoint"])
 @pytest.mark.parametrize("bc", [(W.PERIODIC, W.PERIODIC), (W.ZERO_GRADIENT, W.ZERO_GRADIENT)])
-def test_row_marching_kernel_ragged_sampled(bc):
+def test_row_marching_kernel_ragged_sampled(bc, rk):
     """A 1500 x 1300 grid is large enough for the row-marching stage kernel; neither
     size is a multiple of the block width (128) or of the row runs, so partial blocks
-    and runs cut short by the last row are checked at sampled cells and edges."""
+    (and the x row buffer's halo of their last active thread) and runs cut short by
+    the last row are checked at sampled cells and edges, for both integrators."""
     w = W.random_blocks(1500, 1300, seed=31, bc=bc)
     w.dx = w.dy = 1.0 / 1500
     w.dt = 0.2 * w.dx / 2.2
     w.tau = 2 * w.dt
-    _sampled_check(w, 3, 40, seed=5, edges=True)
+    _sampled_check(w, 3, 40, seed=5, edges=True, rk=rk)
 
 
 def test_taylor_green_4096_conservation():
