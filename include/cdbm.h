@@ -137,8 +137,9 @@ cdbm_status cdbm_init(cdbm_ctx *ctx, const double *rho, const double *ux, const 
  * grid (ny = 1) small enough for one thread-block cluster (at most 16 x 64 cells for
  * CDBM_FP64, 16 x 256 for the single-precision states) instead runs all nsteps in
  * one persistent launch with its state in the cluster's shared memory; the results
- * are the same bit for bit.  Asynchronous; a non-physical state is reported by the
- * next cdbm_sync.
+ * are the same bit for bit for the single-precision states and the same to rounding
+ * for CDBM_FP64, whose cluster kernel splits each cell over four threads.
+ * Asynchronous; a non-physical state is reported by the next cdbm_sync.
  */
 cdbm_status cdbm_step(cdbm_ctx *ctx, int nsteps);
 

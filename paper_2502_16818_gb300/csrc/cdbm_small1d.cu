@@ -8,8 +8,9 @@
 // stage buffers, reads the stencil halo of its edge cells from the neighbouring
 // CTAs' shared memory (distributed shared memory of the cluster), and the stages
 // are separated by the cluster barrier, a hardware barrier over the co-scheduled
-// CTAs (no software spin-wait).  The per-cell arithmetic is that of the flat stage
-// kernel in the same order, so the result is the same bit for bit.
+// CTAs (no software spin-wait).  In single precision the per-cell arithmetic is
+// that of the flat stage kernel in the same order, so the result is the same bit for
+// bit; the FP64 variant splits a cell over four threads (split_stage).
 #include <cooperative_groups.h>
 
 #include "cdbm_stage.cuh"
@@ -122,6 +123,149 @@ __global__ void __launch_bounds__(256) small1d_kernel(TS *f, int nsteps, const S
     }
 }
 
+// FP64 variant with the work of a cell split over four threads, one per velocity
+// group: thread 4c + g of the CTA handles group g of cell c.  A stage of one cell
+// is a chain of dependent FP64 instructions whose latency, not throughput, bounds a
+// small grid (one warp per SM); splitting the cell shortens the chain about fourfold.
+// The four threads exchange their group components (s0, sx, sy) by warp shuffles and
+// each forms the moments, primitive variables and the shared part of the
+// equilibrium with the operations of conserved(), primitives() and equilibrium() in
+// the same order; each then builds and updates its own group's four velocities.
+// The compiler may fuse a multiply and an add differently than in the
+// one-thread-per-cell kernels, so the two agree to rounding, not bit for bit.
+__device__ __forceinline__ void split_stage(const cg::cluster_group &cl, const double *src, const double *base,
+                                            double *dst, const StageArgs &a, bool with_base, int chunk, int rank,
+                                            int x0, int len, unsigned *flag)
+{
+    const int t = threadIdx.x;
+    const int g = t & 3;                              // velocity group of this thread
+    const int lx0 = t >> 2;
+    const bool live = lx0 < len;
+    const int lx = live ? lx0 : len - 1;              // idle threads mirror the last cell
+    const int gx = x0 + lx;
+    const int nx = a.nx;
+    double q[4], bs[4], up2[4], up1[4], dn1[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        q[j] = src[(4 * g + j) * chunk + lx];
+        bs[j] = with_base ? base[(4 * g + j) * chunk + lx] : 0.0;
+    }
+    const bool inner = lx >= 2 && lx + 2 < len;
+    const int xm2 = neighbour(gx - 2, nx, a.bc_x), xm1 = neighbour(gx - 1, nx, a.bc_x);
+    const int xp1 = neighbour(gx + 1, nx, a.bc_x), xp2 = neighbour(gx + 2, nx, a.bc_x);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int i = 4 * g + j;
+        const int sx = dirx(i);
+        if (sx == 0) {
+            up2[j] = up1[j] = dn1[j] = 0.0;
+        } else if (inner) {
+            const double *p = src + i * chunk + lx;
+            up2[j] = p[sx > 0 ? -2 : 2];
+            up1[j] = p[sx > 0 ? -1 : 1];
+            dn1[j] = p[sx > 0 ? 1 : -1];
+        } else {
+            up2[j] = cluster_value(cl, src, chunk, rank, i, sx > 0 ? xm2 : xp2);
+            up1[j] = cluster_value(cl, src, chunk, rank, i, sx > 0 ? xm1 : xp1);
+            dn1[j] = cluster_value(cl, src, chunk, rank, i, sx > 0 ? xp1 : xm1);
+        }
+    }
+    // group components, as conserved()
+    double c0, cx, cy;
+    if ((g & 1) == 0) {
+        cx = q[0] - q[2];
+        cy = q[1] - q[3];
+        c0 = (q[0] + q[2]) + (q[1] + q[3]);
+    } else {
+        const double e = q[0] + q[3], w = q[1] + q[2];
+        cx = e - w;
+        cy = (q[0] + q[1]) - (q[2] + q[3]);
+        c0 = e + w;
+    }
+    const int lane0 = (t & 31) & ~3;
+    double S0[4], SX[4], SY[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        S0[h] = __shfl_sync(0xffffffffu, c0, lane0 + h);
+        SX[h] = __shfl_sync(0xffffffffu, cx, lane0 + h);
+        SY[h] = __shfl_sync(0xffffffffu, cy, lane0 + h);
+    }
+    const ModelConsts &m = a.m;
+    Prim s;
+    s.q.rho = (S0[0] + S0[1]) + (S0[2] + S0[3]);
+    s.q.jx = fma(m.c[3], SX[3], fma(m.c[2], SX[2], fma(m.c[1], SX[1], m.c[0] * SX[0])));
+    s.q.jy = fma(m.c[3], SY[3], fma(m.c[2], SY[2], fma(m.c[1], SY[1], m.c[0] * SY[0])));
+    s.q.E = fma(m.w[3], S0[3], fma(m.w[2], S0[2], fma(m.w[1], S0[1], m.w[0] * S0[0])));
+    const double r = rcp64(s.q.rho);
+    s.ux = s.q.jx * r;
+    s.uy = s.q.jy * r;
+    s.jyuy = s.q.jy * s.uy;
+    s.ru2 = fma(s.q.jx, s.ux, s.jyuy);
+    s.p = (s.q.E - s.ru2) * m.invK;
+    s.T = s.p * r;
+    if (live && g == 0 && !(positive_finite(s.q.rho) && positive_finite(s.p))) atomicOr(flag, kFlagNonPhys);
+    // this group's part of equilibrium()
+    const EqBlocks &B = a.eq;
+    const double ux2 = s.ux * s.ux, uy2 = s.uy * s.uy, u2 = ux2 + uy2;
+    const double m1416 = fma(s.T, fma(m.Kp6, s.ru2, m.twoKp2 * s.p), s.ru2 * u2);
+    const double W4 = fma(m.Kp4, s.T, u2);
+    const double d57 = fma(s.q.jx, s.ux, -s.jyuy);
+    const double m6 = s.q.jx * s.uy;
+    const double *S = B.S + 4 * g;
+    const double *V = B.V + 4 * g;
+    const double e0 = fma(S[3], m1416, fma(S[2], s.ru2, fma(S[1], s.q.E, S[0] * s.q.rho)));
+    const double ex = s.q.jx * fma(V[3], s.T, fma(V[2], uy2, fma(V[1], ux2, V[0])));
+    const double ey = s.q.jy * fma(V[3], s.T, fma(V[1], uy2, fma(V[2], ux2, V[0])));
+    double heq[4];
+    if ((g & 1) == 0) {
+        const double dq = d57 * fma(B.B1[g + 1], W4, B.B1[g]);        // g = 0: a, g = 2: c
+        rebuild_axis(heq, e0, dq, ex, ey);
+    } else {
+        const double qq = m6 * fma(B.B2[g], W4, B.B2[g - 1]);         // g = 1: b, g = 3: d
+        rebuild_diag(heq, e0, qq, ex, ey);
+    }
+    double o[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int i = 4 * g + j;
+        o[j] = fma(a.a_self, q[j], heq[j]);
+        if (with_base) o[j] = fma(a.a_base, bs[j], o[j]);
+        if (dirx(i) != 0) o[j] = fma(-a.lx[g], nnd(up2[j], up1[j], q[j], dn1[j]), o[j]);
+    }
+    if (live) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dst[(4 * g + j) * chunk + lx] = o[j];
+    }
+}
+
+__global__ void __launch_bounds__(256) small1d_split_kernel(double *f, int nsteps, const StageArgs a0,
+                                                            const StageArgs a1, unsigned *flag, int chunk)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *s0 = reinterpret_cast<double *>(smem_raw);
+    double *s1 = s0 + kNV * chunk;
+    const cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int nx = a0.nx;
+    const int x0 = rank * chunk;
+    const int len = nx - x0 < chunk ? (nx - x0 > 0 ? nx - x0 : 0) : chunk;
+    for (int k = threadIdx.x; k < kNV * len; k += blockDim.x) {
+        const int i = k / len, lx = k - i * len;
+        s0[i * chunk + lx] = f[(size_t)i * nx + x0 + lx];
+    }
+    cl.sync();
+    for (int s = 0; s < nsteps; ++s) {
+        split_stage(cl, s0, nullptr, s1, a0, false, chunk, rank, x0, len, flag);
+        cl.sync();
+        split_stage(cl, s1, s0, s0, a1, true, chunk, rank, x0, len, flag);
+        cl.sync();
+    }
+    for (int k = threadIdx.x; k < kNV * len; k += blockDim.x) {
+        const int i = k / len, lx = k - i * len;
+        f[(size_t)i * nx + x0 + lx] = s0[i * chunk + lx];
+    }
+}
+
 template <typename TS, bool kDF>
 void *small1d_func() { return (void *)small1d_kernel<TS, kDF>; }
 
@@ -129,7 +273,7 @@ void *small1d_func_of(int prec)
 {
     if (prec == CDBM_FP32_DF64) return small1d_func<float, true>();
     if (prec == CDBM_FP32_BULK) return small1d_func<float, false>();
-    return small1d_func<double, false>();
+    return (void *)small1d_split_kernel;
 }
 
 }  // namespace
@@ -150,7 +294,9 @@ Small1D small1d_config(const StageArgs &a, int prec)
     const int chunk = (a.nx + cluster - 1) / cluster;
     cluster = (a.nx + chunk - 1) / chunk;            // no empty CTAs
     const size_t smem = 2 * kNV * (size_t)chunk * storage_bytes(prec);
-    int threads = ((chunk + 31) / 32) * 32;
+    // FP64: four threads per cell (split_stage), all cells of the CTA in one pass
+    const int per_cell = prec == CDBM_FP64 ? 4 : 1;
+    int threads = ((per_cell * chunk + 31) / 32) * 32;
     if (threads > 256) threads = 256;
     void *func = small1d_func_of(prec);
     if (cluster > 8 && cudaFuncSetAttribute(func, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {

