@@ -90,11 +90,16 @@ def test_batch_result_independent_of_tile(precision):
 
 
 def test_batch_matches_single_grid_path():
-    from paper_2502_16818_gb300 import Solver
+    """Each tube of an FP64 batch equals the same tube run alone with one launch per
+    stage, bit for bit: both use the same per-cell operations.  (The single-grid
+    cluster kernel for small FP64 tubes splits a cell over four threads and agrees
+    only to rounding, so it is switched off here.)"""
+    from paper_2502_16818_gb300 import Solver, cdbm
     tubes = tubes_small(n=6, seed=6, steps=50)
     b, out = run_batch(tubes, 50)
     for t, w in enumerate(tubes):
         s = Solver.from_workload(w)
+        cdbm.cdbm_set_small_grid_path(s.ctx, 0)
         s.init(w.rho, w.ux, w.uy, w.T)
         s.step(50)
         single = [x.cpu().numpy()[0] for x in s.macros()]
