@@ -70,9 +70,14 @@ struct MomBar {
 // step.  With r = 1/rho, u = j r, ru2 = j.u, P = (E - ru2)/K, T = P r.
 // The forward values r = 1/rho, u, j_y u_y, rho u^2, P and T come from the caller
 // (primitives() of the forward stage, the same refined reciprocal).
-__device__ __forceinline__ MomBar equilibrium_vjp(const EqBlocks &B, const ModelConsts &m, double jx, double jy,
-                                                  double r, double ux, double uy, double jyuy, double ru2,
-                                                  double P, double T, const double ob[kNV])
+// With oheq != nullptr it also returns *oheq = sum_i ob_i out_i, the cotangent
+// applied to the equilibrium itself: the rebuild is a linear butterfly, so that sum
+// is the dot product of the transposed group components (s0b, sxb, syb, qb) with
+// the forward components (s0, sx, sy, q), and the 16 outputs are never formed.
+__device__ __forceinline__ MomBar equilibrium_vjp(const EqBlocks &B, const ModelConsts &m, double rho, double E,
+                                                  double jx, double jy, double r, double ux, double uy, double jyuy,
+                                                  double ru2, double P, double T, const double ob[kNV],
+                                                  double *oheq = nullptr)
 {
     // forward values
     const double ux2 = ux * ux, uy2 = uy * uy, u2 = ux2 + uy2;
@@ -104,6 +109,8 @@ __device__ __forceinline__ MomBar equilibrium_vjp(const EqBlocks &B, const Model
 
     double rhob = 0.0, jxb = 0.0, jyb = 0.0, Eb = 0.0;
     double ru2b = 0.0, m1416b = 0.0, Tb = 0.0, ux2b = 0.0, uy2b = 0.0, W4b = 0.0;
+    const double m1416 = oheq ? fma(T, Y, ru2 * u2) : 0.0;
+    double dot = 0.0;
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
         const double *S = B.S + 4 * g;
@@ -116,6 +123,12 @@ __device__ __forceinline__ MomBar equilibrium_vjp(const EqBlocks &B, const Model
         // sx = jx (V0 + V1 ux2 + V2 uy2 + V3 T), sy = jy (V0 + V2 ux2 + V1 uy2 + V3 T)
         const double cx = fma(V[3], T, fma(V[2], uy2, fma(V[1], ux2, V[0])));
         const double cy = fma(V[3], T, fma(V[1], uy2, fma(V[2], ux2, V[0])));
+        if (oheq) {
+            const double s0 = fma(S[3], m1416, fma(S[2], ru2, fma(S[1], E, S[0] * rho)));
+            dot = fma(s0b[g], s0, dot);
+            dot = fma(sxb[g], jx * cx, dot);
+            dot = fma(syb[g], jy * cy, dot);
+        }
         jxb = fma(cx, sxb[g], jxb);
         jyb = fma(cy, syb[g], jyb);
         const double cxb = jx * sxb[g], cyb = jy * syb[g];
@@ -128,6 +141,7 @@ __device__ __forceinline__ MomBar equilibrium_vjp(const EqBlocks &B, const Model
     const double bB = fma(B.B2[1], W4, B.B2[0]), bD = fma(B.B2[3], W4, B.B2[2]);
     const double d57b = fma(bA, qb[0], bC * qb[2]);
     const double m6b = fma(bB, qb[1], bD * qb[3]);
+    if (oheq) *oheq = fma(d57, d57b, fma(m6, m6b, dot));   // + sum of qb_g q_g
     W4b = d57 * fma(B.B1[1], qb[0], B.B1[3] * qb[2]) + m6 * fma(B.B2[1], qb[1], B.B2[3] * qb[3]);
     // m6 = jx uy;  d57 = jx ux - jyuy
     double uxb = 0.0, uyb = 0.0, jyuyb = 0.0;
@@ -239,13 +253,13 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_stage_kernel(const double
         unsigned nonphys = 0;                              // the forward stage already reported it
         const Prim pr = primitives<false>(f, a.m, 0.0, 0.0, &nonphys);
         const Cons &q = pr.q;
-        double heq[kNV];
-        equilibrium(a.eq, a.m, q.rho, q.E, q.jx, q.jy, pr.ux, pr.uy, pr.ru2, pr.jyuy, pr.p, pr.T, heq);
+        // tau term: sum_i o_i (gamma h g_i - heq_i) / tau, with sum_i o_i heq_i from the VJP
+        double og = 0.0, oheq = 0.0;
 #pragma unroll
-        for (int i = 0; i < kNV; ++i) tau_part = fma(o[i], fma(gamma_h, f[i], -heq[i]), tau_part);
-        tau_part *= inv_tau;
-        const MomBar w = equilibrium_vjp(a.eq, a.m, q.jx, q.jy, pr.r, pr.ux, pr.uy, pr.jyuy, pr.ru2, pr.p, pr.T,
-                                         o);
+        for (int i = 0; i < kNV; ++i) og = fma(o[i], f[i], og);
+        const MomBar w = equilibrium_vjp(a.eq, a.m, q.rho, q.E, q.jx, q.jy, pr.r, pr.ux, pr.uy, pr.jyuy, pr.ru2,
+                                         pr.p, pr.T, o, &oheq);
+        tau_part = fma(gamma_h, og, -oheq) * inv_tau;
 
         int xs[5];
 #pragma unroll
@@ -310,8 +324,8 @@ __global__ void __launch_bounds__(128) init_vjp_kernel(const FieldArgs a, const 
         unsigned nonphys = 0;
         const Prim pr = primitives<false>(f, a.m, 0.0, 0.0, &nonphys);
         const Cons &q = pr.q;
-        const MomBar w = equilibrium_vjp(a.eq, a.m, q.jx, q.jy, pr.r, pr.ux, pr.uy, pr.jyuy, pr.ru2, pr.p, pr.T,
-                                         o);
+        const MomBar w = equilibrium_vjp(a.eq, a.m, q.rho, q.E, q.jx, q.jy, pr.r, pr.ux, pr.uy, pr.jyuy, pr.ru2,
+                                         pr.p, pr.T, o);
         // m = (rho, rho u_x, rho u_y, rho (u^2 + K T)) of the fields
         const double u = q.jx / q.rho, v = q.jy / q.rho;
         const double T = (q.E - fma(q.jx, u, q.jy * v)) / (a.m.K * q.rho);
