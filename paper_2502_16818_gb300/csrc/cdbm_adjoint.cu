@@ -268,14 +268,31 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_stage_kernel(const double
 #pragma unroll
         for (int k = -2; k <= 2; ++k) ys[k + 2] = neighbour(y + k, ny, 0);
 
+        // moment part of the VJP per velocity: rho_bar + v . j_bar + (|v|^2 + eta^2) E_bar,
+        // formed per group as t +- c jx_bar +- c jy_bar with t = rho_bar + w_g E_bar
+        double mb[kNV];
+#pragma unroll
+        for (int grp = 0; grp < 4; ++grp) {
+            const double t = fma(w.E, a.m.w[grp], w.rho);
+            const double ax = w.jx * a.m.c[grp], ay = w.jy * a.m.c[grp];
+            double *q = mb + 4 * grp;
+            if ((grp & 1) == 0) {                    // (1,0), (0,1), (-1,0), (0,-1)
+                q[0] = t + ax;
+                q[1] = t + ay;
+                q[2] = t - ax;
+                q[3] = t - ay;
+            } else {                                 // (1,1), (-1,1), (-1,-1), (1,-1)
+                const double pp = ax + ay, pm = ax - ay;
+                q[0] = t + pp;
+                q[1] = t - pm;
+                q[2] = t - pp;
+                q[3] = t + pm;
+            }
+        }
 #pragma unroll
         for (int i = 0; i < kNV; ++i) {
             const int grp = i >> 2;
-            const double vx = dirx(i) * a.m.c[grp], vy = diry(i) * a.m.c[grp];
-            double gb = fma(a.a_self, o[i], w.rho);
-            gb = fma(w.jx, vx, gb);
-            gb = fma(w.jy, vy, gb);
-            gb = fma(w.E, a.m.w[grp], gb);
+            double gb = fma(a.a_self, o[i], mb[i]);
             const double *gp = g + i * P, *op = ob + i * P;
             if (dirx(i) != 0) {
                 const int s = dirx(i);
