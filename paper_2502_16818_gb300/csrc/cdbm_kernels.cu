@@ -542,11 +542,20 @@ StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count
     const size_t cells = (size_t)a.nx * a.ny;
     const unsigned xblocks = (unsigned)((a.nx + kStageThreads - 1) / kStageThreads);
     // Row-marching kernel when runs of at least 8 rows still give two full waves of
-    // blocks; runs grow to 32 rows while at least 8 waves remain.
+    // blocks; runs grow to 32 rows while at least 8 waves remain.  On smaller grids
+    // (a 512^2 sound wave has 4 blocks across) runs of 4 or 2 rows are used if they
+    // give two waves: each run repeats a 2-row prologue, but the x and y differences
+    // are still computed once per cell.
     const size_t wave = (size_t)sm_count * stage_min_blocks(prec == CDBM_FP32_DF64);
     int R = 8;
     while (R < 32 && (size_t)xblocks * ((a.ny + 2 * R - 1) / (2 * R)) >= 8 * wave) R *= 2;
-    const bool march = !flat && a.ny >= 16 && (size_t)xblocks * ((a.ny + 7) / 8) >= 2 * wave;
+    bool march = !flat && a.ny >= 16 && (size_t)xblocks * ((a.ny + 7) / 8) >= 2 * wave;
+    for (int r = 4; !march && !flat && a.ny >= 16 && r >= 2; r /= 2) {
+        if ((size_t)xblocks * ((a.ny + r - 1) / r) >= 2 * wave) {
+            march = true;
+            R = r;
+        }
+    }
     L.func = prec == CDBM_FP32_DF64   ? stage_func<float, true>(march, with_base, flat)
              : prec == CDBM_FP32_BULK ? stage_func<float, false>(march, with_base, flat)
                                       : stage_func<double, false>(march, with_base, flat);
