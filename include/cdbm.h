@@ -203,9 +203,11 @@ cdbm_status cdbm_adjoint_forward(cdbm_ctx *ctx, int nsteps, int every);
  * writes dL/drho0, dL/du_x0, dL/du_y0, dL/dT0 of the fields the state was
  * initialised from by cdbm_init ([ny][nx] each; NULL skips) and dL/dtau (host
  * scalar; NULL skips).  Each segment between checkpoints is recomputed forward
- * (min(every, nsteps) states held at once), then swept backward through the
- * transposed stages.  Synchronous.  Errors: CDBM_EINVAL without a recorded run that
- * ends at the current state; CDBM_ENOMEM. */
+ * (min(every, nsteps) states held at once, plus as many Runge-Kutta stage-1
+ * states when the allocator can provide them; without those the sweep recomputes
+ * each stage-1 state), then swept backward through the transposed stages.
+ * Synchronous.  Errors: CDBM_EINVAL without a recorded run that ends at the
+ * current state; CDBM_ENOMEM. */
 cdbm_status cdbm_adjoint_backward(cdbm_ctx *ctx, const double *fbar, double *grad_rho, double *grad_ux,
                                   double *grad_uy, double *grad_T, double *grad_tau);
 

@@ -824,6 +824,22 @@ cdbm_status cdbm_adjoint_backward(cdbm_ctx *c, const double *fbar, double *grad_
     for (void *p : bufs) ok = ok && p;
     cdbm_status st = CDBM_OK;
     if (!ok) st = set_err(c, CDBM_ENOMEM, "adjoint work buffers (%d states) failed", seglen + 2);
+    // Optional: the stage-1 states of a segment, kept from its recomputation so the
+    // backward sweep does not recompute them (one stage launch per step less, one
+    // more segment of memory).  Without the memory the sweep recomputes them.
+    std::vector<double *> seg1;
+    if (!st) {
+        for (int j = 0; j < seglen; ++j) {
+            double *p = (double *)ctx_alloc(c, fb);
+            if (!p) break;
+            seg1.push_back(p);
+        }
+        if ((int)seg1.size() < seglen) {
+            for (double *p : seg1) ctx_free(c, p, fb);
+            seg1.clear();
+        }
+    }
+    const bool keep1 = !seg1.empty();
     const double h = c->dt / c->tau, inv_tau = 1.0 / c->tau;
     if (!st && (cuda_check(c, cudaMemcpyAsync(B, fbar, fb, cudaMemcpyDefault, c->stream), "cotangent copy") ||
                 cuda_check(c, cudaMemsetAsync(acc, 0, sizeof(double) * (nacc + 1), c->stream), "acc clear")))
@@ -832,16 +848,20 @@ cdbm_status cdbm_adjoint_backward(cdbm_ctx *c, const double *fbar, double *grad_
     for (int sgi = nseg - 1; sgi >= 0 && !st; --sgi) {
         const int len = (sgi + 1) * every <= nsteps ? every : nsteps - sgi * every;
         seg[0] = (double *)c->ckpt[sgi];
-        for (int j = 0; j + 1 < len && !st; ++j) {
-            cudaError_t e = launch_stage(c->launch[0], seg[j], nullptr, G1, c->stage[0], c->flag, c->stream);
-            if (e == cudaSuccess)
-                e = launch_stage(c->launch[1], G1, seg[j], seg[j + 1], c->stage[1], c->flag, c->stream);
+        for (int j = 0; j < len && !st; ++j) {
+            if (!keep1 && j + 1 == len) break;
+            double *g1 = keep1 ? seg1[j] : G1;
+            cudaError_t e = launch_stage(c->launch[0], seg[j], nullptr, g1, c->stage[0], c->flag, c->stream);
+            if (e == cudaSuccess && j + 1 < len)
+                e = launch_stage(c->launch[1], g1, seg[j], seg[j + 1], c->stage[1], c->flag, c->stream);
             st = cuda_check(c, e, "adjoint recompute");
         }
         for (int j = len - 1; j >= 0 && !st; --j) {
-            cudaError_t e = launch_stage(c->launch[0], seg[j], nullptr, G1, c->stage[0], c->flag, c->stream);
+            const double *g1 = keep1 ? seg1[j] : G1;
+            cudaError_t e = keep1 ? cudaSuccess
+                                  : launch_stage(c->launch[0], seg[j], nullptr, G1, c->stage[0], c->flag, c->stream);
             if (e == cudaSuccess)   // stage 2: f^{n+1} = f^n/2 + f1/2 + dt/2 L(f1)
-                e = launch_adjoint_stage(G1, B, nullptr, 0.0, B1, c->stage[1], 0.5 * h, inv_tau, c->adj_limiter, acc,
+                e = launch_adjoint_stage(g1, B, nullptr, 0.0, B1, c->stage[1], 0.5 * h, inv_tau, c->adj_limiter, acc,
                                          c->stream);
             if (e == cudaSuccess)   // stage 1: f1 = f^n + dt L(f^n); plus the f^n/2 of stage 2
                 e = launch_adjoint_stage(seg[j], B1, B, 0.5, B, c->stage[0], h, inv_tau, c->adj_limiter, acc, c->stream);
@@ -859,6 +879,7 @@ cdbm_status cdbm_adjoint_backward(cdbm_ctx *c, const double *fbar, double *grad_
     }
     if (!st) st = cuda_check(c, cudaStreamSynchronize(c->stream), "adjoint sync");
     for (size_t k = 0; k < bufs.size(); ++k) ctx_free(c, bufs[k], k == 3 ? sizeof(double) * (nacc + 1) : fb);
+    for (double *p : seg1) ctx_free(c, p, fb);
     return st;
 }
 
