@@ -91,7 +91,8 @@ typedef enum {
                           /* enters the stage update                               */
     CDBM_FP32_DF64 = 2    /* as CDBM_FP32_BULK, with the sums, moment shift and    */
                           /* equilibrium product in double-float arithmetic (pairs */
-                          /* of floats, ~48-bit significands) on the FP32 pipe     */
+                          /* of floats) on the FP32 pipe, with an absolute error   */
+                          /* of a few 2^-47 of the reference equilibrium F         */
 } cdbm_precision;
 
 /* Time integrator.  The paper names a second-order Runge-Kutta scheme without
