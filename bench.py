@@ -290,7 +290,11 @@ def run_cdbm(a, rank, world, local_rank):
     peak_tflops = 2 * FP64_LANES_PER_CLK_PER_SM * 152 * 2070e6 / 1e12
     instr_rate = FP64_INSTR_PER_CELL_STEP / 2 * cells / (launch_ms * 1e-3)
     hbm_gbs = BYTES_PER_CELL_STEP * cells * a.steps / (ms * 1e-3) / 1e9
-    traffic = TRAFFIC_BYTES_PER_LAUNCH if TRAFFIC_SHA == kernel_sha() else None
+    # the capture scales with the cells only while a plane set exceeds the L2
+    plane_set_bytes = 16 * 8 * cells
+    traffic = None
+    if TRAFFIC_SHA == kernel_sha() and plane_set_bytes >= 1024 * 1024 * 128:
+        traffic = TRAFFIC_BYTES_PER_LAUNCH * cells / 4096 ** 2
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved_tflops / peak_tflops, "traffic": traffic,
                 "kernel": "stage_march_kernel (RK stages 1 and 2, mean per launch)",
@@ -304,7 +308,8 @@ def run_cdbm(a, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "taylor_green_%dx%d_fp64" % (a.n, a.n), "nx": w.nx, "ny": w.ny,
                    "I": w.I, "tau": w.tau, "dt": w.dt, "vset": [w.vg, w.eg], "precision": "fp64",
-                   "rk": "tvd2", "l2": "state 2.15 GB per buffer >> 129 MB L2, no flush",
+                   "rk": "tvd2",
+                   "l2": "state %.3g GB per buffer vs 129 MB L2, no flush" % (plane_set_bytes / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "gpu_launches": 2 * a.steps,
         "clocks": clocks,
