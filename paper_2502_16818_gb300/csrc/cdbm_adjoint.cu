@@ -80,7 +80,7 @@ __device__ __forceinline__ MomBar equilibrium_vjp(const EqBlocks &B, const Model
                                                   double *oheq = nullptr)
 {
     // forward values
-    const double ux2 = ux * ux, uy2 = uy * uy, u2 = ux2 + uy2;
+    const double ux2 = ux * ux, uy2 = uy * uy, u2 = ux2 + uy2, dlt = ux2 - uy2;
     const double Y = fma(m.Kp6, ru2, m.twoKp2 * P);
     const double W4 = fma(m.Kp4, T, u2);
     const double d57 = fma(jx, ux, -jyuy);
@@ -108,33 +108,34 @@ __device__ __forceinline__ MomBar equilibrium_vjp(const EqBlocks &B, const Model
     }
 
     double rhob = 0.0, jxb = 0.0, jyb = 0.0, Eb = 0.0;
-    double ru2b = 0.0, m1416b = 0.0, Tb = 0.0, ux2b = 0.0, uy2b = 0.0, W4b = 0.0;
+    double ru2b = 0.0, m1416b = 0.0, Tb = 0.0, u2vb = 0.0, dltb = 0.0, W4b = 0.0;
     const double m1416 = oheq ? fma(T, Y, ru2 * u2) : 0.0;
     double dot = 0.0;
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
         const double *S = B.S + 4 * g;
-        const double *V = B.V + 4 * g;
+        const double *W = B.Vc + 4 * g;
         // s0 = S0 rho + S1 E + S2 ru2 + S3 m1416
         rhob = fma(S[0], s0b[g], rhob);
         Eb = fma(S[1], s0b[g], Eb);
         ru2b = fma(S[2], s0b[g], ru2b);
         m1416b = fma(S[3], s0b[g], m1416b);
-        // sx = jx (V0 + V1 ux2 + V2 uy2 + V3 T), sy = jy (V0 + V2 ux2 + V1 uy2 + V3 T)
-        const double cx = fma(V[3], T, fma(V[2], uy2, fma(V[1], ux2, V[0])));
-        const double cy = fma(V[3], T, fma(V[1], uy2, fma(V[2], ux2, V[0])));
+        // sx = jx px, sy = jy py with px, py = cm +/- W3 dlt and cm = W0 + W1 T + W2 u2
+        const double cm = fma(W[2], u2, fma(W[1], T, W[0]));
+        const double px = fma(W[3], dlt, cm), py = fma(-W[3], dlt, cm);
+        const double pxb = jx * sxb[g], pyb = jy * syb[g];
         if (oheq) {
             const double s0 = fma(S[3], m1416, fma(S[2], ru2, fma(S[1], E, S[0] * rho)));
             dot = fma(s0b[g], s0, dot);
-            dot = fma(sxb[g], jx * cx, dot);
-            dot = fma(syb[g], jy * cy, dot);
+            dot = fma(pxb, px, dot);    // sxb sx = (jx sxb) px
+            dot = fma(pyb, py, dot);
         }
-        jxb = fma(cx, sxb[g], jxb);
-        jyb = fma(cy, syb[g], jyb);
-        const double cxb = jx * sxb[g], cyb = jy * syb[g];
-        ux2b = fma(V[1], cxb, fma(V[2], cyb, ux2b));
-        uy2b = fma(V[2], cxb, fma(V[1], cyb, uy2b));
-        Tb = fma(V[3], cxb + cyb, Tb);
+        jxb = fma(px, sxb[g], jxb);
+        jyb = fma(py, syb[g], jyb);
+        const double cb = pxb + pyb;
+        dltb = fma(W[3], pxb - pyb, dltb);
+        u2vb = fma(W[2], cb, u2vb);
+        Tb = fma(W[1], cb, Tb);
     }
     // dq_a = d57 (B1_0 + B1_1 W4), dq_c = d57 (B1_2 + B1_3 W4); q_b, q_d likewise with m6
     const double bA = fma(B.B1[1], W4, B.B1[0]), bC = fma(B.B1[3], W4, B.B1[2]);
@@ -160,9 +161,9 @@ __device__ __forceinline__ MomBar equilibrium_vjp(const EqBlocks &B, const Model
     ru2b = fma(m.Kp6, Yb, ru2b);
     u2b = fma(ru2, m1416b, u2b);
     double Pb = m.twoKp2 * Yb;
-    // u2 = ux2 + uy2; ux2 = ux^2; uy2 = uy^2
-    ux2b += u2b;
-    uy2b += u2b;
+    // u2 = ux2 + uy2, dlt = ux2 - uy2; ux2 = ux^2; uy2 = uy^2
+    u2b += u2vb;
+    const double ux2b = u2b + dltb, uy2b = u2b - dltb;
     uxb = fma(2.0 * ux, ux2b, uxb);
     uyb = fma(2.0 * uy, uy2b, uyb);
     // T = P r

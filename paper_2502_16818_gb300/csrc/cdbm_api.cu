@@ -263,6 +263,10 @@ cdbm_status build_blocks(const cdbm_vset &vs, double I, ModelConsts &m, EqBlocks
         eq.V[g * 4 + 1] = fv * (v[1] + v[2]);
         eq.V[g * 4 + 2] = fv * (v[1] + v[3]);
         eq.V[g * 4 + 3] = fv * ((K + 2.0) * v[1] + 3.0 * v[2] + v[3]);
+        eq.Vc[g * 4 + 0] = eq.V[g * 4 + 0];
+        eq.Vc[g * 4 + 1] = eq.V[g * 4 + 3];
+        eq.Vc[g * 4 + 2] = 0.5 * (eq.V[g * 4 + 1] + eq.V[g * 4 + 2]);
+        eq.Vc[g * 4 + 3] = 0.5 * (eq.V[g * 4 + 1] - eq.V[g * 4 + 2]);
     }
     for (int k = 0; k < 4; ++k) {
         eq.B1[k] = 0.25 * B1I[k];
@@ -279,6 +283,7 @@ EqBlocks scaled(const EqBlocks &e, double s)
     for (int k = 0; k < 16; ++k) {
         o.S[k] = s * e.S[k];
         o.V[k] = s * e.V[k];
+        o.Vc[k] = s * e.Vc[k];
     }
     for (int k = 0; k < 4; ++k) {
         o.B1[k] = s * e.B1[k];

@@ -128,22 +128,42 @@ __device__ __forceinline__ Cons conserved(const double f[kNV], const ModelConsts
     return r;
 }
 
-__device__ __forceinline__ void rebuild_axis(double *o, double s0, double dq, double sx, double sy)
+// Members of an axis group (E N W S) from the group sum s0, the quadrupole dq and the
+// odd components j_x px, j_y py (the products fused into the sums).
+__device__ __forceinline__ void rebuild_axis(double *o, double s0, double dq, double jx, double px,
+                                             double jy, double py)
 {
     const double A = s0 + dq, B = s0 - dq;
-    o[0] = A + sx;
-    o[2] = A - sx;
-    o[1] = B + sy;
-    o[3] = B - sy;
+    o[0] = fma(jx, px, A);
+    o[2] = fma(-jx, px, A);
+    o[1] = fma(jy, py, B);
+    o[3] = fma(-jy, py, B);
 }
 
-__device__ __forceinline__ void rebuild_diag(double *o, double s0, double q, double sx, double sy)
+// Members of a diagonal group (NE NW SW SE), likewise.
+__device__ __forceinline__ void rebuild_diag(double *o, double s0, double q, double jx, double px,
+                                             double jy, double py)
 {
-    const double P = s0 + q, Q = s0 - q, U = sx + sy, V = sx - sy;
+    const double sy = jy * py;
+    const double P = s0 + q, Q = s0 - q, U = fma(jx, px, sy), V = fma(jx, px, -sy);
     o[0] = P + U;   // NE
     o[2] = P - U;   // SW
     o[1] = Q - V;   // NW
     o[3] = Q + V;   // SE
+}
+
+// One group's members of the scaled equilibrium: s0 from the scalar block, the odd
+// polynomials from their common part and half difference (Vc), the quadrupole qv
+// (dq of an axis group, q of a diagonal one) given.
+__device__ __forceinline__ void equilibrium_group(const EqBlocks &B, int g, double s0, double qv,
+                                                  double jx, double jy, double T, double u2,
+                                                  double dlt, double *o)
+{
+    const double *W = B.Vc + 4 * g;
+    const double cm = fma(W[2], u2, fma(W[1], T, W[0]));
+    const double px = fma(W[3], dlt, cm), py = fma(-W[3], dlt, cm);
+    if ((g & 1) == 0) rebuild_axis(o, s0, qv, jx, px, jy, py);
+    else rebuild_diag(o, s0, qv, jx, px, jy, py);
 }
 
 // Scaled equilibrium out_i = scale * f_eq,i (Eqs. 4-7) in factored form: the raw
@@ -159,29 +179,26 @@ __device__ __forceinline__ void equilibrium(const EqBlocks &B, const ModelConsts
                                             double ru2, double jyuy, double P, double T,
                                             double out[kNV], const double *s0_shift = nullptr)
 {
-    const double ux2 = ux * ux, uy2 = uy * uy, u2 = ux2 + uy2;
+    const double ux2 = ux * ux, uy2 = uy * uy, u2 = ux2 + uy2, dlt = ux2 - uy2;
     const double m1416 = fma(T, fma(m.Kp6, ru2, m.twoKp2 * P), ru2 * u2);  // m14 + m16
     const double W4 = fma(m.Kp4, T, u2);
     const double d57 = fma(jx, ux, -jyuy);                                  // m5 - m7
     const double m6 = jx * uy;
-    double s0[4], sx[4], sy[4];
+    double s0[4];
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
         const double *S = B.S + 4 * g;
-        const double *V = B.V + 4 * g;
         s0[g] = fma(S[3], m1416, fma(S[2], ru2, fma(S[1], E, S[0] * rho)));
         if (kShift) s0[g] -= s0_shift[g];
-        sx[g] = jx * fma(V[3], T, fma(V[2], uy2, fma(V[1], ux2, V[0])));
-        sy[g] = jy * fma(V[3], T, fma(V[1], uy2, fma(V[2], ux2, V[0])));
     }
     const double dqa = d57 * fma(B.B1[1], W4, B.B1[0]);
     const double dqc = d57 * fma(B.B1[3], W4, B.B1[2]);
     const double qb = m6 * fma(B.B2[1], W4, B.B2[0]);
     const double qd = m6 * fma(B.B2[3], W4, B.B2[2]);
-    rebuild_axis(out + 0, s0[0], dqa, sx[0], sy[0]);
-    rebuild_diag(out + 4, s0[1], qb, sx[1], sy[1]);
-    rebuild_axis(out + 8, s0[2], dqc, sx[2], sy[2]);
-    rebuild_diag(out + 12, s0[3], qd, sx[3], sy[3]);
+    equilibrium_group(B, 0, s0[0], dqa, jx, jy, T, u2, dlt, out + 0);
+    equilibrium_group(B, 1, s0[1], qb, jx, jy, T, u2, dlt, out + 4);
+    equilibrium_group(B, 2, s0[2], dqc, jx, jy, T, u2, dlt, out + 8);
+    equilibrium_group(B, 3, s0[3], qd, jx, jy, T, u2, dlt, out + 12);
 }
 
 template <typename TS>

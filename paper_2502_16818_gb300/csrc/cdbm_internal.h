@@ -31,11 +31,16 @@ constexpr int kNV = 16;     // discrete velocities, Eq. (2)
 //   sy_g = j_y (V[g][0] + V[g][2] u_x^2 + V[g][1] u_y^2 + V[g][3] T)
 //          (m8 = j_x (u^2 + (K+2)T), m10 = j_x (u_x^2 + 3T), m12 = j_x (u_y^2 + T), and
 //           the mirror images for y)
+// The kernels evaluate the two odd polynomials from their common part and half
+// difference, Vc[g] = (V[g][0], V[g][3], (V[g][1] + V[g][2]) / 2, (V[g][1] - V[g][2]) / 2):
+//   V[g][0] + V[g][3] T + Vc[g][2] u^2 +/- Vc[g][3] (u_x^2 - u_y^2),
+// and fuse the products with j_x, j_y into the rebuild of the four members.
 struct EqBlocks {
     double S[16];   // row-major 4x4
     double B1[4];   // row-major 2x2
     double B2[4];   // row-major 2x2
     double V[16];   // row-major 4x4
+    double Vc[16];  // per group: V0, V3, (V1 + V2) / 2, (V1 - V2) / 2
 };
 
 struct ModelConsts {

@@ -206,24 +206,17 @@ __device__ __forceinline__ void split_stage(const cg::cluster_group &cl, const d
     if (live && g == 0 && !(positive_finite(s.q.rho) && positive_finite(s.p))) atomicOr(flag, kFlagNonPhys);
     // this group's part of equilibrium()
     const EqBlocks &B = a.eq;
-    const double ux2 = s.ux * s.ux, uy2 = s.uy * s.uy, u2 = ux2 + uy2;
+    const double ux2 = s.ux * s.ux, uy2 = s.uy * s.uy, u2 = ux2 + uy2, dlt = ux2 - uy2;
     const double m1416 = fma(s.T, fma(m.Kp6, s.ru2, m.twoKp2 * s.p), s.ru2 * u2);
     const double W4 = fma(m.Kp4, s.T, u2);
     const double d57 = fma(s.q.jx, s.ux, -s.jyuy);
     const double m6 = s.q.jx * s.uy;
     const double *S = B.S + 4 * g;
-    const double *V = B.V + 4 * g;
     const double e0 = fma(S[3], m1416, fma(S[2], s.ru2, fma(S[1], s.q.E, S[0] * s.q.rho)));
-    const double ex = s.q.jx * fma(V[3], s.T, fma(V[2], uy2, fma(V[1], ux2, V[0])));
-    const double ey = s.q.jy * fma(V[3], s.T, fma(V[1], uy2, fma(V[2], ux2, V[0])));
+    const double qv = (g & 1) == 0 ? d57 * fma(B.B1[g + 1], W4, B.B1[g])       // g = 0: a, g = 2: c
+                                   : m6 * fma(B.B2[g], W4, B.B2[g - 1]);       // g = 1: b, g = 3: d
     double heq[4];
-    if ((g & 1) == 0) {
-        const double dq = d57 * fma(B.B1[g + 1], W4, B.B1[g]);        // g = 0: a, g = 2: c
-        rebuild_axis(heq, e0, dq, ex, ey);
-    } else {
-        const double qq = m6 * fma(B.B2[g], W4, B.B2[g - 1]);         // g = 1: b, g = 3: d
-        rebuild_diag(heq, e0, qq, ex, ey);
-    }
+    equilibrium_group(B, g, e0, qv, s.q.jx, s.q.jy, s.T, u2, dlt, heq);
     double o[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
