@@ -34,14 +34,14 @@ METRIC = "cell-updates/s and HBM GB/s vs FP64 plain on same GB300 at stated L2 e
 UNIT = "cell-updates/s"
 
 # FP64 work of the fused (row-marching) stage kernels per cell.  Instructions: ncu
-# sm__inst_executed_pipe_fp64 per warp of 32 cells (stage 1: 254, stage 2: 270).
-# Flops, counted from the kernel source with an FMA as two flops: stage 1: 376,
-# stage 2: 408 (each x difference computed once per cell and shared through the row
+# sm__inst_executed_pipe_fp64 per warp of 32 cells (stage 1: 246, stage 2: 262).
+# Flops, counted from the kernel source with an FMA as two flops: stage 1: 367,
+# stage 2: 399 (each x difference computed once per cell and shared through the row
 # buffer; the halo recomputation of the block-edge threads is not counted).  Bytes
 # per cell-step: stage 1 reads f^n and writes f1 (128 + 128 B); stage 2 reads f1 and
 # f^n and writes f^n+1 (384 B).
-FP64_INSTR_PER_CELL_STEP = 524
-FP64_FLOPS_PER_CELL_STEP = 784
+FP64_INSTR_PER_CELL_STEP = 508
+FP64_FLOPS_PER_CELL_STEP = 766
 BYTES_PER_CELL_STEP = 640
 FP64_LANES_PER_CLK_PER_SM = 2       # 1.25 TFLOP/s nominal FP64 / (2 flops x 152 SMs x 2.07 GHz)
 
