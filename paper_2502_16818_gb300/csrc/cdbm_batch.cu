@@ -89,13 +89,13 @@ __device__ __forceinline__ void tube_stage(const TS *g, const TS *base, TS *out,
         } else {
             double f[kNV];
 #pragma unroll
-            for (int i = 0; i < kNV; ++i) f[i] = (double)fs[i];
+            for (int i = 0; i < kNV; ++i) f[i] = widen(fs[i]);
             const Prim s = primitives<kSingle<TS>>(f, C.m, t.rhoF, t.EF, flag);
             double h[kNV];
             equilibrium<kSingle<TS>>(C.eq[kStage], C.m, s.q.rho, s.q.E, s.q.jx, s.q.jy, s.ux, s.uy, s.ru2,
                                      s.jyuy, s.p, s.T, h, t.sF[kStage]);
 #pragma unroll
-            for (int i = 0; i < kNV; ++i) heq[i] = (TS)h[i];
+            for (int i = 0; i < kNV; ++i) heq[i] = narrow<TS>(h[i]);
         }
 #pragma unroll
         for (int i = 0; i < kNV; ++i) {

@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "cdbm_convert.h"
 #include "cdbm_internal.h"
 
 namespace cdbm {
@@ -68,14 +69,17 @@ __device__ __forceinline__ double nnd(double u2, double u1, double c, double d1)
 }
 
 // Single-precision twins of minmod() and nnd() for the single-precision states.
-// minmod: the smaller magnitude with X's sign when the sign bits agree, else 0.  A
-// zero argument gives a zero result either way (min(|X|, |Y|) = 0), and equal
+// minmod: min.xorsign.abs gives min(|X|, |Y|) with the sign bit set iff the sign
+// bits of X and Y differ; clamping it at zero and giving it X's sign yields the
+// smaller magnitude with X's sign when the sign bits agree, else 0 (three
+// instructions).  A zero argument gives a zero result either way, and equal
 // magnitudes with equal signs are the same value, so this is the Eq. (16) reading
 // of the double version; only the sign of an exact zero result may differ.
 __device__ __forceinline__ float minmod(float X, float Y)
 {
-    const float m = copysignf(fminf(fabsf(X), fabsf(Y)), X);
-    return (__float_as_int(X) ^ __float_as_int(Y)) >= 0 ? m : 0.0f;
+    float r;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(X), "f"(Y));
+    return copysignf(fmaxf(r, 0.0f), X);
 }
 
 __device__ __forceinline__ float nnd(float u2, float u1, float c, float d1)
@@ -205,6 +209,16 @@ template <typename TS>
 constexpr bool kSingle = std::is_same<TS, float>::value;
 
 __device__ __forceinline__ double fma_t(double x, double y, double z) { return fma(x, y, z); }
+
+// Storage value to double and double to storage value; the single-precision
+// conversions run on the integer pipes (cdbm_convert.h).
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ double widen(float v) { return widen_f32(v); }
+template <typename TS>
+__device__ __forceinline__ TS narrow(double v)
+{
+    if constexpr (kSingle<TS>) return narrow_f64(v); else return v;
+}
 __device__ __forceinline__ float fma_t(float x, float y, float z) { return fmaf(x, y, z); }
 
 // Per-cell macroscopic quantities of a stage: conserved moments (in double), then

@@ -41,13 +41,13 @@ __device__ __forceinline__ void stage_equilibrium(const StageArgs &a, const TS f
     } else {
         double f[kNV];
 #pragma unroll
-        for (int i = 0; i < kNV; ++i) f[i] = (double)fs[i];
+        for (int i = 0; i < kNV; ++i) f[i] = widen(fs[i]);
         const Prim s = primitives<kSingle<TS>>(f, a.m, a.rhoF, a.EF, flag);
         double h[kNV];
         equilibrium<kSingle<TS>>(a.eq, a.m, s.q.rho, s.q.E, s.q.jx, s.q.jy, s.ux, s.uy, s.ru2, s.jyuy,
                                  s.p, s.T, h, a.sF);
 #pragma unroll
-        for (int i = 0; i < kNV; ++i) heq[i] = (TS)h[i];
+        for (int i = 0; i < kNV; ++i) heq[i] = narrow<TS>(h[i]);
     }
 }
 
