@@ -73,8 +73,9 @@ typedef struct {
 } cdbm_vset;
 
 /* Optional device-memory allocator (for example a caching allocator).  alloc
- * returns device memory of at least `bytes` usable on `stream`, or NULL; free
- * releases it.  With no allocator the library uses cudaMallocAsync/cudaFreeAsync
+ * returns device memory of at least `bytes` usable on `stream`, aligned to at
+ * least 16 bytes, or NULL (a block that is not so aligned is handed back to free
+ * and counts as NULL); free releases it.  With no allocator the library uses cudaMallocAsync/cudaFreeAsync
  * on the context stream. */
 typedef struct {
     void *(*alloc)(size_t bytes, void *stream, void *user);
@@ -147,6 +148,13 @@ cdbm_status cdbm_step(cdbm_ctx *ctx, int nsteps);
 /* Enables (default) or disables the persistent cluster path of cdbm_step for small
  * 1-D grids; disabled, those grids step with one launch per stage like any other. */
 cdbm_status cdbm_set_small_grid_path(cdbm_ctx *ctx, int enable);
+
+/* Enables (default) or disables the row-marching stage kernels on 2-D grids, which
+ * carry the y differences of a run of rows in shared memory (and, for
+ * CDBM_FP32_DF64, advance two columns per thread with packed FP32x2 arithmetic);
+ * disabled, every stage runs one cell per thread.  Both give the same results bit
+ * for bit; the switch serves cross-checks and timing.  EINVAL for a NULL context. */
+cdbm_status cdbm_set_row_marching(cdbm_ctx *ctx, int enable);
 
 /*
  * cdbm_macros -- writes rho, u_x, u_y, T of the current state ([ny][nx] each,

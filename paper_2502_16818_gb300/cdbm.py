@@ -25,7 +25,7 @@ CDBM_ADJ_LIMITER_EXACT, CDBM_ADJ_LIMITER_FROZEN_RATIO, CDBM_ADJ_LIMITER_FROZEN =
 CDBM_RK2_TVD, CDBM_RK2_MIDPOINT = 0, 1
 
 #: every entry point declared in include/cdbm.h
-EXPORTS = ("cdbm_create", "cdbm_set_rk", "cdbm_init", "cdbm_step", "cdbm_set_small_grid_path", "cdbm_macros",
+EXPORTS = ("cdbm_create", "cdbm_set_rk", "cdbm_init", "cdbm_step", "cdbm_set_small_grid_path", "cdbm_set_row_marching", "cdbm_macros",
            "cdbm_tne", "cdbm_conserved_sums", "cdbm_get_state", "cdbm_set_state", "cdbm_state_ptr", "cdbm_time",
            "cdbm_sync", "cdbm_last_error", "cdbm_destroy", "cdbm_step_noalloc",
            "cdbm_batch_create", "cdbm_batch_init", "cdbm_batch_step", "cdbm_batch_autotune",
@@ -85,6 +85,7 @@ def load(path: str | None = None):
         "cdbm_init": ([ctx, _vp, _vp, _vp, _vp], ctypes.c_int),
         "cdbm_step": ([ctx, ctypes.c_int], ctypes.c_int),
         "cdbm_set_small_grid_path": ([ctx, ctypes.c_int], ctypes.c_int),
+        "cdbm_set_row_marching": ([ctx, ctypes.c_int], ctypes.c_int),
         "cdbm_macros": ([ctx, _vp, _vp, _vp, _vp], ctypes.c_int),
         "cdbm_tne": ([ctx, _vp], ctypes.c_int),
         "cdbm_conserved_sums": ([ctx, _dp], ctypes.c_int),
@@ -160,6 +161,11 @@ def cdbm_step(ctx, nsteps):
 def cdbm_set_small_grid_path(ctx, enable):
     lib = load()
     _check(lib, ctx, lib.cdbm_set_small_grid_path(ctx, int(bool(enable))))
+
+
+def cdbm_set_row_marching(ctx, enable):
+    lib = load()
+    _check(lib, ctx, lib.cdbm_set_row_marching(ctx, int(bool(enable))))
 
 
 def cdbm_macros(ctx, rho, ux, uy, T):

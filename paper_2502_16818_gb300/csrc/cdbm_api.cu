@@ -74,6 +74,7 @@ struct cdbm_ctx {
     cudaGraphExec_t graph;
     Small1D small;                // persistent cluster path for small 1-D grids
     bool small_enabled;
+    bool march_enabled;       // row-marching stage kernels on 2-D grids
 
     // adjoint record of the last cdbm_adjoint_forward
     int adj_steps, adj_every;     // steps recorded, checkpoint interval (0: none)
@@ -116,7 +117,14 @@ cdbm_status cuda_check(cdbm_ctx *c, cudaError_t e, const char *what)
 
 void *ctx_alloc(cdbm_ctx *c, size_t bytes)
 {
-    if (c->user_alloc) return c->alloc.alloc(bytes, (void *)c->stream, c->alloc.user);
+    if (c->user_alloc) {
+        void *p = c->alloc.alloc(bytes, (void *)c->stream, c->alloc.user);
+        if (p && ((uintptr_t)p & 15u)) {         // the kernels move 8- and 16-byte words
+            c->alloc.free(p, bytes, (void *)c->stream, c->alloc.user);
+            return nullptr;
+        }
+        return p;
+    }
     void *p = nullptr;
     if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
         cudaGetLastError();
@@ -344,7 +352,7 @@ void build_stages(cdbm_ctx *c)
         a.bc_x = c->grid.bc_x;
         a.bc_y = c->grid.bc_y;
         fill_df_consts(a);
-        c->launch[s] = stage_launch_config(a, r.with_base, c->sm_count, c->precision);
+        c->launch[s] = stage_launch_config(a, r.with_base, c->sm_count, c->precision, c->march_enabled);
     }
     c->small = small1d_config(c->stage[0], c->precision);
 }
@@ -454,6 +462,7 @@ cdbm_status cdbm_create(const cdbm_grid *grid, const cdbm_vset *vset, double I, 
     c->precision = precision;
     c->rk = CDBM_RK2_TVD;
     c->small_enabled = true;
+    c->march_enabled = true;
     c->stream = (cudaStream_t)cuda_stream;
     c->user_alloc = allocator && allocator->alloc && allocator->free;
     if (c->user_alloc) c->alloc = *allocator;
@@ -606,6 +615,18 @@ cdbm_status cdbm_set_small_grid_path(cdbm_ctx *c, int enable)
     if (!c) return CDBM_EINVAL;
     if (c->err) return c->err;
     c->small_enabled = enable != 0;
+    return CDBM_OK;
+}
+
+cdbm_status cdbm_set_row_marching(cdbm_ctx *c, int enable)
+{
+    if (!c) return CDBM_EINVAL;
+    if (c->err) return c->err;
+    if ((enable != 0) != c->march_enabled) {
+        c->march_enabled = enable != 0;
+        drop_graph(c);
+        build_stages(c);
+    }
     return CDBM_OK;
 }
 

@@ -82,6 +82,12 @@ __device__ __forceinline__ float minmod(float X, float Y)
     return copysignf(fmaxf(r, 0.0f), X);
 }
 
+// minmod of the two lanes of packed pairs (no packed form of min.xorsign.abs).
+__device__ __forceinline__ float2 minmod(float2 X, float2 Y)
+{
+    return make_float2(minmod(X.x, Y.x), minmod(X.y, Y.y));
+}
+
 __device__ __forceinline__ float nnd(float u2, float u1, float c, float d1)
 {
     const float a = c - u1;

@@ -21,12 +21,32 @@
 // the single-precision state from double to double-float trades each FP64
 // instruction for 4-15 FP32 instructions that the four FP32 issue slots per SM
 // absorb.
+//
+// Lanes.  Every function is written once over a lane type L: float computes one
+// cell, float2 two cells with the packed FP32x2 instructions of sm_100 and later
+// (one instruction issue for two IEEE operations).  The packed operations round
+// each half exactly as the scalar ones do, so the two-cell form gives, cell by
+// cell, the same bits as the one-cell form.
 #pragma once
 
 #include "cdbm_device.cuh"
 
 namespace cdbm {
 
+// ---- lane operations: float or float2, each IEEE round-to-nearest ----
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float neg(float a) { return -a; }
+__device__ __forceinline__ float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 add_rn(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub_rn(float2 a, float2 b) { return __fadd2_rn(a, neg(b)); }
+__device__ __forceinline__ float2 mul_rn(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma_rn(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+template <typename L>
+using dfl = DFv<L>;
 using df = DFPair;
 
 __host__ __device__ inline df df_from(double v)
@@ -35,146 +55,172 @@ __host__ __device__ inline df df_from(double v)
     return {h, (float)(v - (double)h)};
 }
 
-__device__ __forceinline__ df df_of(float v) { return {v, 0.0f}; }
+template <typename L>
+__device__ __forceinline__ dfl<L> df_of(L v)
+{
+    if constexpr (std::is_same<L, float>::value) return {v, 0.0f}; else return {v, make_float2(0.0f, 0.0f)};
+}
 
-__device__ __forceinline__ float df_to_float(df x) { return __fadd_rn(x.hi, x.lo); }
+template <typename L>
+__device__ __forceinline__ L df_to_float(dfl<L> x) { return add_rn(x.hi, x.lo); }
 
 // s + e = a + b exactly.
-__device__ __forceinline__ df two_sum(float a, float b)
+template <typename L>
+__device__ __forceinline__ dfl<L> two_sum(L a, L b)
 {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    const L s = add_rn(a, b);
+    const L bb = sub_rn(s, a);
+    const L e = add_rn(sub_rn(a, sub_rn(s, bb)), sub_rn(b, bb));
     return {s, e};
 }
 
 // s + e = a + b exactly, for |a| >= |b| (or a = 0).
-__device__ __forceinline__ df fast_two_sum(float a, float b)
+template <typename L>
+__device__ __forceinline__ dfl<L> fast_two_sum(L a, L b)
 {
-    const float s = __fadd_rn(a, b);
-    const float e = __fsub_rn(b, __fsub_rn(s, a));
+    const L s = add_rn(a, b);
+    const L e = sub_rn(b, sub_rn(s, a));
     return {s, e};
 }
 
 // x + y with an error of a few 2^-48 (|x| + |y|): exact sum of the high parts, the
 // low parts added in float, renormalised once.
-__device__ __forceinline__ df df_add(df x, df y)
+template <typename L>
+__device__ __forceinline__ dfl<L> df_add(dfl<L> x, dfl<L> y)
 {
-    const df s = two_sum(x.hi, y.hi);
-    return fast_two_sum(s.hi, __fadd_rn(__fadd_rn(x.lo, y.lo), s.lo));
+    const dfl<L> s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, add_rn(add_rn(x.lo, y.lo), s.lo));
 }
 
-__device__ __forceinline__ df df_neg(df x) { return {-x.hi, -x.lo}; }
-__device__ __forceinline__ df df_sub(df x, df y) { return df_add(x, df_neg(y)); }
+template <typename L>
+__device__ __forceinline__ dfl<L> df_neg(dfl<L> x) { return {neg(x.hi), neg(x.lo)}; }
+template <typename L>
+__device__ __forceinline__ dfl<L> df_sub(dfl<L> x, dfl<L> y) { return df_add(x, df_neg(y)); }
 
 // x * y, unnormalised: the exact error of hi * hi plus the cross terms (x.lo * y.lo
 // is below the df rounding and dropped).
-__device__ __forceinline__ df df_mul(df x, df y)
+template <typename L>
+__device__ __forceinline__ dfl<L> df_mul(dfl<L> x, dfl<L> y)
 {
-    const float p = __fmul_rn(x.hi, y.hi);
-    float e = __fmaf_rn(x.hi, y.hi, -p);
-    e = __fmaf_rn(x.hi, y.lo, e);
-    e = __fmaf_rn(x.lo, y.hi, e);
+    const L p = mul_rn(x.hi, y.hi);
+    L e = fma_rn(x.hi, y.hi, neg(p));
+    e = fma_rn(x.hi, y.lo, e);
+    e = fma_rn(x.lo, y.hi, e);
     return {p, e};
 }
 
-__device__ __forceinline__ df df_fma(df a, df b, df c) { return df_add(df_mul(a, b), c); }
+template <typename L>
+__device__ __forceinline__ dfl<L> df_fma(dfl<L> a, dfl<L> b, dfl<L> c) { return df_add(df_mul(a, b), c); }
+
+__device__ __forceinline__ float rcp_estimate(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float2 rcp_estimate(float2 x) { return make_float2(rcp_estimate(x.x), rcp_estimate(x.y)); }
 
 // 1 / x: hardware float estimate (about 2^-23 relative) refined by one Newton step
 // in df64, r + r (1 - x r), which squares the relative error.
-__device__ __forceinline__ df df_rcp(df x)
+template <typename L>
+__device__ __forceinline__ dfl<L> df_rcp(dfl<L> x)
 {
-    float r0;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(x.hi));
-    const df r = df_of(r0);
-    const df e = df_sub(df_of(1.0f), df_mul(x, r));
+    const dfl<L> r = df_of(rcp_estimate(x.hi));
+    L one;
+    if constexpr (std::is_same<L, float>::value) one = 1.0f; else one = make_float2(1.0f, 1.0f);
+    const dfl<L> e = df_sub(df_of(one), df_mul(x, r));
     return df_add(r, df_mul(r, e));
 }
 
-// true iff v > 0 and finite (bit tests).
+// true iff v > 0 and finite (bit tests), in every lane.
 __device__ __forceinline__ bool positive_finite_f(float v)
 {
     const int b = __float_as_int(v);
     return b > 0 && b < 0x7f800000;
 }
+__device__ __forceinline__ bool positive_finite_f(float2 v) { return positive_finite_f(v.x) && positive_finite_f(v.y); }
 
-__device__ __forceinline__ void rebuild_axis_f(float *o, float s0, float dq, float sx, float sy)
+template <typename L>
+__device__ __forceinline__ void rebuild_axis_f(L *o, L s0, L dq, L sx, L sy)
 {
-    const float A = s0 + dq, B = s0 - dq;
-    o[0] = A + sx;
-    o[2] = A - sx;
-    o[1] = B + sy;
-    o[3] = B - sy;
+    const L A = add_rn(s0, dq), B = sub_rn(s0, dq);
+    o[0] = add_rn(A, sx);
+    o[2] = sub_rn(A, sx);
+    o[1] = add_rn(B, sy);
+    o[3] = sub_rn(B, sy);
 }
 
-__device__ __forceinline__ void rebuild_diag_f(float *o, float s0, float q, float sx, float sy)
+template <typename L>
+__device__ __forceinline__ void rebuild_diag_f(L *o, L s0, L q, L sx, L sy)
 {
-    const float P = s0 + q, Q = s0 - q, U = sx + sy, V = sx - sy;
-    o[0] = P + U;
-    o[2] = P - U;
-    o[1] = Q - V;
-    o[3] = Q + V;
+    const L P = add_rn(s0, q), Q = sub_rn(s0, q), U = add_rn(sx, sy), V = sub_rn(sx, sy);
+    o[0] = add_rn(P, U);
+    o[2] = sub_rn(P, U);
+    o[1] = sub_rn(Q, V);
+    o[3] = add_rn(Q, V);
 }
 
-// Scaled equilibrium deviation of one cell of the single-precision state, in df64:
-// heq_i = gamma h (f_eq,i(m(F + g)) - F_i) rounded to float, from the stored
-// deviations g (the same steps as primitives() and equilibrium<true>()).
-__device__ __forceinline__ void df_equilibrium(const DFBlocks &B, const DFModel &d, const DFShift &R,
-                                               const float fs[kNV], float heq[kNV], unsigned *flag)
+// Scaled equilibrium deviation of one cell (or, with L = float2, of two cells) of
+// the single-precision state, in df64: heq_i = gamma h (f_eq,i(m(F + g)) - F_i)
+// rounded to float, from the stored deviations g (the same steps as primitives()
+// and equilibrium<true>()).
+template <typename L>
+__device__ __forceinline__ void df_equilibrium(const DFBlocksT<L> &B, const DFModelT<L> &d, const DFShiftT<L> &R,
+                                               const L fs[kNV], L heq[kNV], unsigned *flag)
 {
-    df s0[4], sx[4], sy[4];
+    dfl<L> s0[4], sx[4], sy[4];
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
-        const float *q = fs + 4 * g;
+        const L *q = fs + 4 * g;
         if ((g & 1) == 0) {
             s0[g] = df_add(two_sum(q[0], q[2]), two_sum(q[1], q[3]));
-            sx[g] = two_sum(q[0], -q[2]);
-            sy[g] = two_sum(q[1], -q[3]);
+            sx[g] = two_sum(q[0], neg(q[2]));
+            sy[g] = two_sum(q[1], neg(q[3]));
         } else {
-            const df e = two_sum(q[0], q[3]), w = two_sum(q[1], q[2]);
+            const dfl<L> e = two_sum(q[0], q[3]), w = two_sum(q[1], q[2]);
             sx[g] = df_sub(e, w);
             sy[g] = df_sub(two_sum(q[0], q[1]), two_sum(q[2], q[3]));
             s0[g] = df_add(e, w);
         }
     }
-    const df rho = df_add(df_add(df_add(s0[0], s0[1]), df_add(s0[2], s0[3])), R.rhoF);
-    df jx = df_mul(d.c[0], sx[0]), jy = df_mul(d.c[0], sy[0]), E = df_add(df_mul(d.w[0], s0[0]), R.EF);
+    const dfl<L> rho = df_add(df_add(df_add(s0[0], s0[1]), df_add(s0[2], s0[3])), R.rhoF);
+    dfl<L> jx = df_mul(d.c[0], sx[0]), jy = df_mul(d.c[0], sy[0]), E = df_add(df_mul(d.w[0], s0[0]), R.EF);
 #pragma unroll
     for (int g = 1; g < 4; ++g) {
         jx = df_fma(d.c[g], sx[g], jx);
         jy = df_fma(d.c[g], sy[g], jy);
         E = df_fma(d.w[g], s0[g], E);
     }
-    const df r = df_rcp(rho);
-    const df ux = df_mul(jx, r), uy = df_mul(jy, r);
-    const df jyuy = df_mul(jy, uy);
-    const df ru2 = df_fma(jx, ux, jyuy);
-    const df P = df_mul(df_sub(E, ru2), d.invK);
-    const df T = df_mul(P, r);
+    const dfl<L> r = df_rcp(rho);
+    const dfl<L> ux = df_mul(jx, r), uy = df_mul(jy, r);
+    const dfl<L> jyuy = df_mul(jy, uy);
+    const dfl<L> ru2 = df_fma(jx, ux, jyuy);
+    const dfl<L> P = df_mul(df_sub(E, ru2), d.invK);
+    const dfl<L> T = df_mul(P, r);
     if (!(positive_finite_f(rho.hi) && positive_finite_f(P.hi))) atomicOr(flag, kFlagNonPhys);
 
-    const df ux2 = df_mul(ux, ux), uy2 = df_mul(uy, uy), u2 = df_add(ux2, uy2), du2 = df_sub(ux2, uy2);
-    const df m1416 = df_fma(T, df_fma(d.Kp6, ru2, df_mul(d.twoKp2, P)), df_mul(ru2, u2));
-    const df W4 = df_fma(d.Kp4, T, u2);
-    const df d57 = df_sub(df_mul(jx, ux), jyuy);
-    const df m6 = df_mul(jx, uy);
-    float c0[4], cx[4], cy[4];
+    const dfl<L> ux2 = df_mul(ux, ux), uy2 = df_mul(uy, uy), u2 = df_add(ux2, uy2), du2 = df_sub(ux2, uy2);
+    const dfl<L> m1416 = df_fma(T, df_fma(d.Kp6, ru2, df_mul(d.twoKp2, P)), df_mul(ru2, u2));
+    const dfl<L> W4 = df_fma(d.Kp4, T, u2);
+    const dfl<L> d57 = df_sub(df_mul(jx, ux), jyuy);
+    const dfl<L> m6 = df_mul(jx, uy);
+    L c0[4], cx[4], cy[4];
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
-        const df *S = B.S + 4 * g;
-        const df s = df_fma(S[3], m1416, df_fma(S[2], ru2, df_fma(S[1], E, df_mul(S[0], rho))));
+        const dfl<L> *S = B.S + 4 * g;
+        const dfl<L> s = df_fma(S[3], m1416, df_fma(S[2], ru2, df_fma(S[1], E, df_mul(S[0], rho))));
         c0[g] = df_to_float(df_sub(s, R.sF[g]));
         // V0 + V1 u_x^2 + V2 u_y^2 + V3 T and its mirror, through the shared part
         // V0 + V3 T + (V1 + V2)/2 u^2 and the odd part (V1 - V2)/2 (u_x^2 - u_y^2)
-        const df cm = df_fma(B.Vs[g], u2, df_fma(B.V3[g], T, B.V0[g]));
-        const df cd = df_mul(B.Vd[g], du2);
+        const dfl<L> cm = df_fma(B.Vs[g], u2, df_fma(B.V3[g], T, B.V0[g]));
+        const dfl<L> cd = df_mul(B.Vd[g], du2);
         cx[g] = df_to_float(df_mul(jx, df_add(cm, cd)));
         cy[g] = df_to_float(df_mul(jy, df_sub(cm, cd)));
     }
-    const float dqa = df_to_float(df_mul(d57, df_fma(B.B1[1], W4, B.B1[0])));
-    const float dqc = df_to_float(df_mul(d57, df_fma(B.B1[3], W4, B.B1[2])));
-    const float qb = df_to_float(df_mul(m6, df_fma(B.B2[1], W4, B.B2[0])));
-    const float qd = df_to_float(df_mul(m6, df_fma(B.B2[3], W4, B.B2[2])));
+    const L dqa = df_to_float(df_mul(d57, df_fma(B.B1[1], W4, B.B1[0])));
+    const L dqc = df_to_float(df_mul(d57, df_fma(B.B1[3], W4, B.B1[2])));
+    const L qb = df_to_float(df_mul(m6, df_fma(B.B2[1], W4, B.B2[0])));
+    const L qd = df_to_float(df_mul(m6, df_fma(B.B2[3], W4, B.B2[2])));
     rebuild_axis_f(heq + 0, c0[0], dqa, cx[0], cy[0]);
     rebuild_diag_f(heq + 4, c0[1], qb, cx[1], cy[1]);
     rebuild_axis_f(heq + 8, c0[2], dqc, cx[2], cy[2]);

@@ -52,27 +52,39 @@ struct ModelConsts {
 };
 
 // Double-float copies of the stage constants for CDBM_FP32_DF64 (each value as the
-// unevaluated sum of two floats; see cdbm_df64.cuh).
-struct DFPair {
-    float hi, lo;
+// unevaluated sum of two floats; see cdbm_df64.cuh).  L is the lane type of the
+// arithmetic: float for one cell, float2 for two cells computed together with the
+// packed FP32x2 instructions (the constants then hold each value twice).
+template <typename L>
+struct DFv {
+    L hi, lo;
 };
-struct DFBlocks {                 // EqBlocks (scaled per stage); the x-odd rows of V as
-    DFPair S[16], B1[4], B2[4];   // V0, V3, (V1 + V2)/2 and (V1 - V2)/2 per group
-    DFPair V0[4], V3[4], Vs[4], Vd[4];
+using DFPair = DFv<float>;
+template <typename L>
+struct DFBlocksT {                // EqBlocks (scaled per stage); the x-odd rows of V as
+    DFv<L> S[16], B1[4], B2[4];   // V0, V3, (V1 + V2)/2 and (V1 - V2)/2 per group
+    DFv<L> V0[4], V3[4], Vs[4], Vd[4];
 };
-struct DFModel {                  // the ModelConsts the equilibrium uses
-    DFPair c[4], w[4];
-    DFPair invK, Kp4, Kp6, twoKp2;
+template <typename L>
+struct DFModelT {                 // the ModelConsts the equilibrium uses
+    DFv<L> c[4], w[4];
+    DFv<L> invK, Kp4, Kp6, twoKp2;
 };
-struct DFShift {                  // reference state of the deviation storage
-    DFPair sF[4];                 // gamma h F_g
-    DFPair rhoF, EF;
+template <typename L>
+struct DFShiftT {                 // reference state of the deviation storage
+    DFv<L> sF[4];                 // gamma h F_g
+    DFv<L> rhoF, EF;
 };
-struct DFConsts {
-    DFBlocks b;
-    DFModel m;
-    DFShift r;
+template <typename L>
+struct DFConstsT {
+    DFBlocksT<L> b;
+    DFModelT<L> m;
+    DFShiftT<L> r;
 };
+using DFBlocks = DFBlocksT<float>;
+using DFModel = DFModelT<float>;
+using DFShift = DFShiftT<float>;
+using DFConsts = DFConstsT<float>;
 
 // One Runge-Kutta stage: out = a_base * base + a_self * g + eq(g) - sum_r l_r D_r(g),
 // i.e. alpha f^n + beta g + gamma dt L(g) with a_self = beta - gamma h, the
@@ -94,6 +106,9 @@ struct StageArgs {
     double sF[4];
     double rhoF, EF;
     DFConsts d;                   // df64 copies (CDBM_FP32_DF64)
+    DFConstsT<float2> d2;         // the same, each value twice (two-column kernel)
+    float2 a_base_f2, a_self_f2;  // a_base_f, a_self_f, lx_f, ly_f twice
+    float2 lx_f2[4], ly_f2[4];
     int nx, ny;
     int bc_x, bc_y;
 };
@@ -146,7 +161,9 @@ struct StageLaunch {
     void *func;
     dim3 grid, block;
 };
-StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count, int prec);
+// allow_march = false keeps 2-D grids on the one-cell-per-thread stage kernel.
+StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count, int prec,
+                                bool allow_march = true);
 cudaError_t launch_stage(const StageLaunch &L, const void *g, const void *base, void *out,
                          const StageArgs &a, unsigned *flag, cudaStream_t s);
 

@@ -287,6 +287,131 @@ __global__ void __launch_bounds__(kStageThreads, stage_min_blocks(kDF))
     }
 }
 
+// Row-marching stage of the df64 state with two columns per thread.  Thread t of
+// block b owns the columns x0 = 2 (b blockDim + t) and x1 = x0 + 1 (x1 = x0 for an
+// odd last column, computed twice and stored once) and applies every operation of
+// stage_march_kernel<float, kBase, true> to both cells at once with the packed
+// FP32x2 instructions: lane by lane the same IEEE operations, so each cell gets the
+// bits of the one-column kernel, with about half the instruction issues for the
+// arithmetic, which bounds that kernel.  kVec: nx is even, so the pair (x0, x1) of a
+// row is 8-byte aligned and moves as one float2.
+constexpr int kMarch2MinBlocks = 3;
+
+template <bool kBase, bool kVec>
+__global__ void __launch_bounds__(kStageThreads, kMarch2MinBlocks)
+    stage_march2_kernel(const float *__restrict__ g, const float *base, float *out, const StageArgs a,
+                        unsigned *flag)
+{
+    __shared__ float2 carry_u[kNY][kStageThreads];
+    __shared__ float2 carry_n[kNY][kStageThreads];
+    const int nx = a.nx, ny = a.ny;
+    const int tid = threadIdx.x;
+    const int x0 = 2 * (int)(blockIdx.x * blockDim.x + tid);
+    if (x0 >= nx) return;                             // no block barriers below
+    const bool two = x0 + 1 < nx;
+    const int x1 = two ? x0 + 1 : x0;
+    const int R = (ny + gridDim.y - 1) / gridDim.y;
+    const int y0 = blockIdx.y * R;
+    const int y1 = y0 + R < ny ? y0 + R : ny;
+    if (y0 >= y1) return;
+    const size_t P = (size_t)nx * ny;
+    const int m2a = neighbour(x0 - 2, nx, a.bc_x), m1a = neighbour(x0 - 1, nx, a.bc_x);
+    const int p1a = neighbour(x0 + 1, nx, a.bc_x), p2a = neighbour(x0 + 2, nx, a.bc_x);
+    const int m2b = neighbour(x1 - 2, nx, a.bc_x), m1b = neighbour(x1 - 1, nx, a.bc_x);
+    const int p1b = neighbour(x1 + 1, nx, a.bc_x), p2b = neighbour(x1 + 2, nx, a.bc_x);
+    const float2 half2 = make_float2(0.5f, 0.5f);
+    // the two cells of a row, and an arbitrary pair of columns of a row
+    auto ld = [&](const float *p) -> float2 {
+        if constexpr (kVec) return __ldg(reinterpret_cast<const float2 *>(p + x0));
+        else return make_float2(__ldg(p + x0), __ldg(p + x1));
+    };
+    auto ld_at = [&](const float *p, int ca, int cb) -> float2 { return make_float2(__ldg(p + ca), __ldg(p + cb)); };
+
+    // prologue: U_{y0} and N_{y0 - 1} for s = +1, N_{y0} for s = -1
+    {
+        const size_t r0 = (size_t)y0 * nx;
+        const size_t rm1 = (size_t)neighbour(y0 - 1, ny, a.bc_y) * nx;
+        const size_t rm2 = (size_t)neighbour(y0 - 2, ny, a.bc_y) * nx;
+        const size_t rp1 = (size_t)neighbour(y0 + 1, ny, a.bc_y) * nx;
+#pragma unroll
+        for (int k = 0; k < kNY; ++k) {
+            const int i = yvel(k);
+            const float *gp = g + i * P;
+            const float2 f0 = ld(gp + r0), fm1 = ld(gp + rm1);
+            if (diry(i) > 0) {
+                const float2 u = sub_rn(f0, fm1);
+                const float2 um = sub_rn(fm1, ld(gp + rm2));
+                carry_u[k][tid] = u;
+                carry_n[k][tid] = minmod(u, um);
+            } else {
+                const float2 u = sub_rn(f0, ld(gp + rp1));
+                const float2 um = sub_rn(fm1, f0);
+                carry_u[k][tid] = u;
+                carry_n[k][tid] = minmod(um, u);
+            }
+        }
+    }
+
+    for (int y = y0; y < y1; ++y) {
+        const size_t row = (size_t)y * nx;
+        float2 fs[kNV], o[kNV], heq[kNV];
+#pragma unroll
+        for (int i = 0; i < kNV; ++i) fs[i] = ld(g + i * P + row);
+        df_equilibrium(a.d2.b, a.d2.m, a.d2.r, fs, heq, flag);
+#pragma unroll
+        for (int i = 0; i < kNV; ++i) {
+            o[i] = fma_rn(a.a_self_f2, fs[i], heq[i]);
+            if (kBase) o[i] = fma_rn(a.a_base_f2, ld(base + i * P + row), o[i]);
+            if (dirx(i) != 0) {
+                const float *gp = g + i * P + row;
+                const bool pos = dirx(i) > 0;
+                const float2 u2 = pos ? ld_at(gp, m2a, m2b) : ld_at(gp, p2a, p2b);
+                const float2 u1 = pos ? ld_at(gp, m1a, m1b) : ld_at(gp, p1a, p1b);
+                const float2 d1 = pos ? ld_at(gp, p1a, p1b) : ld_at(gp, m1a, m1b);
+                const float2 av = sub_rn(fs[i], u1);
+                const float2 bv = sub_rn(d1, fs[i]);
+                const float2 ev = sub_rn(u1, u2);
+                const float2 t = sub_rn(minmod(bv, av), minmod(av, ev));
+                o[i] = fma_rn(neg(a.lx_f2[i >> 2]), fma_rn(half2, t, av), o[i]);
+            }
+        }
+        const size_t rp1 = (size_t)neighbour(y + 1, ny, a.bc_y) * nx;
+        const size_t rp2 = (size_t)neighbour(y + 2, ny, a.bc_y) * nx;
+#pragma unroll
+        for (int k = 0; k < kNY; ++k) {
+            const int i = yvel(k);
+            const float *gp = g + i * P;
+            const float2 u = carry_u[k][tid];
+            const float2 n = carry_n[k][tid];
+            float2 t;
+            if (diry(i) > 0) {
+                const float2 un = sub_rn(ld(gp + rp1), fs[i]);              // U_{y+1}
+                const float2 nn = minmod(un, u);                            // N_y
+                t = sub_rn(nn, n);
+                carry_u[k][tid] = un;
+                carry_n[k][tid] = nn;
+            } else {
+                const float2 un = sub_rn(ld(gp + rp1), ld(gp + rp2));       // U_{y+1}
+                const float2 nn = minmod(u, un);                            // N_{y+1}
+                t = sub_rn(n, nn);
+                carry_u[k][tid] = un;
+                carry_n[k][tid] = nn;
+            }
+            o[i] = fma_rn(neg(a.ly_f2[i >> 2]), fma_rn(half2, t, u), o[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < kNV; ++i) {
+            float *op = out + i * P + row;
+            if constexpr (kVec) {
+                *reinterpret_cast<float2 *>(op + x0) = o[i];
+            } else {
+                op[x0] = o[i].x;
+                if (two) op[x1] = o[i].y;
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------ macros (K3)
 
 template <typename TS>
@@ -457,11 +582,19 @@ unsigned grid_for(size_t cells, int threads)
     return (unsigned)(b < 1 ? 1 : (b > 1048576 ? 1048576 : b));
 }
 
+void *stage_march2_func(bool with_base, bool vec)
+{
+    if (with_base) return vec ? (void *)stage_march2_kernel<true, true> : (void *)stage_march2_kernel<true, false>;
+    return vec ? (void *)stage_march2_kernel<false, true> : (void *)stage_march2_kernel<false, false>;
+}
+
 template <typename TS, bool kDF>
 void *stage_func(bool march, bool with_base, bool flat)
 {
-    if (march)
-        return with_base ? (void *)stage_march_kernel<TS, true, kDF> : (void *)stage_march_kernel<TS, false, kDF>;
+    if constexpr (!kDF) {   // the df64 state marches with stage_march2_kernel
+        if (march)
+            return with_base ? (void *)stage_march_kernel<TS, true, false> : (void *)stage_march_kernel<TS, false, false>;
+    }
     if (with_base)
         return flat ? (void *)stage_kernel<TS, true, true, kDF> : (void *)stage_kernel<TS, true, false, kDF>;
     return flat ? (void *)stage_kernel<TS, false, true, kDF> : (void *)stage_kernel<TS, false, false, kDF>;
@@ -535,36 +668,42 @@ cudaError_t launch_field_means(const double *rho, const double *T, size_t n, dou
     return cudaGetLastError();
 }
 
-StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count, int prec)
+StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count, int prec, bool allow_march)
 {
     StageLaunch L;
     const bool flat = (a.ny == 1);
     const size_t cells = (size_t)a.nx * a.ny;
-    const unsigned xblocks = (unsigned)((a.nx + kStageThreads - 1) / kStageThreads);
+    // The df64 state marches two columns per thread (stage_march2_kernel).
+    const bool pair = prec == CDBM_FP32_DF64;
+    const int cols = pair ? 2 * kStageThreads : kStageThreads;
+    const unsigned xblocks = (unsigned)((a.nx + cols - 1) / cols);
     // Row-marching kernel when runs of at least 8 rows still give two full waves of
     // blocks; runs grow to 32 rows while at least 8 waves remain.  On smaller grids
     // (a 512^2 sound wave has 4 blocks across) runs of 4 or 2 rows are used if they
     // give two waves: each run repeats a 2-row prologue, but the x and y differences
     // are still computed once per cell.
-    const size_t wave = (size_t)sm_count * stage_min_blocks(prec == CDBM_FP32_DF64);
+    const size_t wave = (size_t)sm_count * (pair ? kMarch2MinBlocks : stage_min_blocks(false));
     int R = 8;
     while (R < 32 && (size_t)xblocks * ((a.ny + 2 * R - 1) / (2 * R)) >= 8 * wave) R *= 2;
-    bool march = !flat && a.ny >= 16 && (size_t)xblocks * ((a.ny + 7) / 8) >= 2 * wave;
-    for (int r = 4; !march && !flat && a.ny >= 16 && r >= 2; r /= 2) {
+    bool march = allow_march && !flat && a.ny >= 16 && (size_t)xblocks * ((a.ny + 7) / 8) >= 2 * wave;
+    for (int r = 4; allow_march && !march && !flat && a.ny >= 16 && r >= 2; r /= 2) {
         if ((size_t)xblocks * ((a.ny + r - 1) / r) >= 2 * wave) {
             march = true;
             R = r;
         }
     }
-    L.func = prec == CDBM_FP32_DF64   ? stage_func<float, true>(march, with_base, flat)
-             : prec == CDBM_FP32_BULK ? stage_func<float, false>(march, with_base, flat)
-                                      : stage_func<double, false>(march, with_base, flat);
     if (march) {
+        L.func = pair ? stage_march2_func(with_base, (a.nx & 1) == 0)
+                 : prec == CDBM_FP32_BULK ? stage_func<float, false>(true, with_base, false)
+                                          : stage_func<double, false>(true, with_base, false);
         L.block = dim3(kStageThreads, 1, 1);
         const unsigned yblocks = (unsigned)((a.ny + R - 1) / R);
         L.grid = dim3(xblocks, yblocks < 65535 ? yblocks : 65535, 1);
         return L;
     }
+    L.func = prec == CDBM_FP32_DF64   ? stage_func<float, true>(false, with_base, flat)
+             : prec == CDBM_FP32_BULK ? stage_func<float, false>(false, with_base, flat)
+                                      : stage_func<double, false>(false, with_base, flat);
     // Small grids: narrower blocks so that more SMs share the cells.
     int threads = kStageThreads;
     while (threads > 32 && cells < (size_t)sm_count * threads * 2) threads >>= 1;
@@ -612,11 +751,47 @@ DFShift df_shift(const double sF[4], double rhoF, double EF)
     return d;
 }
 
+namespace {
+
+DFv<float2> twice(DFPair p) { return {make_float2(p.hi, p.hi), make_float2(p.lo, p.lo)}; }
+
+template <int N>
+void twice_all(const DFPair (&in)[N], DFv<float2> (&out)[N])
+{
+    for (int k = 0; k < N; ++k) out[k] = twice(in[k]);
+}
+
+}  // namespace
+
 void fill_df_consts(StageArgs &a)
 {
     a.d.b = df_blocks(a.eq);
     a.d.m = df_model(a.m);
     a.d.r = df_shift(a.sF, a.rhoF, a.EF);
+    // each value twice for the two-column kernel
+    DFConstsT<float2> &t = a.d2;
+    twice_all(a.d.b.S, t.b.S);
+    twice_all(a.d.b.B1, t.b.B1);
+    twice_all(a.d.b.B2, t.b.B2);
+    twice_all(a.d.b.V0, t.b.V0);
+    twice_all(a.d.b.V3, t.b.V3);
+    twice_all(a.d.b.Vs, t.b.Vs);
+    twice_all(a.d.b.Vd, t.b.Vd);
+    twice_all(a.d.m.c, t.m.c);
+    twice_all(a.d.m.w, t.m.w);
+    t.m.invK = twice(a.d.m.invK);
+    t.m.Kp4 = twice(a.d.m.Kp4);
+    t.m.Kp6 = twice(a.d.m.Kp6);
+    t.m.twoKp2 = twice(a.d.m.twoKp2);
+    twice_all(a.d.r.sF, t.r.sF);
+    t.r.rhoF = twice(a.d.r.rhoF);
+    t.r.EF = twice(a.d.r.EF);
+    a.a_base_f2 = make_float2(a.a_base_f, a.a_base_f);
+    a.a_self_f2 = make_float2(a.a_self_f, a.a_self_f);
+    for (int g = 0; g < 4; ++g) {
+        a.lx_f2[g] = make_float2(a.lx_f[g], a.lx_f[g]);
+        a.ly_f2[g] = make_float2(a.ly_f[g], a.ly_f[g]);
+    }
 }
 
 cudaError_t launch_stage(const StageLaunch &L, const void *g, const void *base, void *out,

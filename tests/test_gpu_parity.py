@@ -465,3 +465,32 @@ def test_small_grid_cluster_path_matches_stage_launches(prec, rk, bc):
             assert d <= 1e-12, (nx, rk, bc, d)
         else:
             assert np.array_equal(states[0], states[1]), (nx, prec, rk, bc)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("shape", [(1026, 600), (1027, 600), (514, 2100)])
+@pytest.mark.parametrize("bc", [(W.PERIODIC, W.PERIODIC), (W.ZERO_GRADIENT, W.ZERO_GRADIENT)])
+def test_row_marching_matches_one_cell_per_thread(prec, shape, bc):
+    """The row-marching stage kernels (y differences carried up runs of rows; FP64
+    also shares the x differences through a row buffer; the df64 state advances two
+    columns per thread with packed FP32x2 arithmetic) and the one-cell-per-thread
+    stage kernel apply the same operations to every cell, so 7 steps agree bit for
+    bit.  The shapes select runs of 8, 4 and 2 rows, even and odd nx (the aligned
+    float2 and the per-column forms of the two-column kernel, and a last thread with
+    one column), and partial blocks and runs."""
+    from paper_2502_16818_gb300 import Solver, cdbm
+    nx, ny = shape
+    w = W.random_blocks(nx, ny, seed=nx + ny, bc=bc)
+    w.dx = w.dy = 1.0 / nx
+    w.dt = 0.2 * w.dx / 2.2
+    w.tau = 2 * w.dt
+    states = []
+    for enable in (1, 0):
+        s = Solver.from_workload(w, precision=prec)
+        cdbm.cdbm_set_row_marching(s.ctx, enable)
+        s.init(w.rho, w.ux, w.uy, w.T)
+        s.step(7)
+        s.sync()
+        states.append(s.state().cpu().numpy())
+        s.close()
+    assert np.array_equal(states[0], states[1]), (prec, shape, bc)
