@@ -19,9 +19,10 @@ constexpr int kStageThreads = 128;
 #ifndef CDBM_STAGE_MIN_BLOCKS
 #define CDBM_STAGE_MIN_BLOCKS 3   // resident stage blocks per SM the register budget must allow
 #endif
-// The df64 stages keep their arithmetic in float registers and hide memory latency
-// better with more warps: 6 blocks of 128 threads per SM (80 registers) measured
-// fastest on the 4096^2 vortex (2.25 ms per step, against 2.47 ms at 3 blocks).
+// The one-cell df64 stage kernel keeps its arithmetic in float registers and hides
+// memory latency better with more warps: 6 blocks of 128 threads per SM (80
+// registers) measured fastest (2.25 ms per 4096^2 vortex step, against 2.47 ms at 3
+// blocks).  Large 2-D df64 grids use the two-column kernel (kMarch2MinBlocks).
 #ifndef CDBM_STAGE_MIN_BLOCKS_DF
 #define CDBM_STAGE_MIN_BLOCKS_DF 6
 #endif
