@@ -289,7 +289,7 @@ cdbm_status cdbm_batch_init(cdbm_batch *b, const double *rho, const double *ux, 
 cdbm_status cdbm_batch_step(cdbm_batch *b, int nsteps);
 
 /* Times the candidate tiles (64/128/256 threads per block x 1, 2, 3, 4 or 6 blocks
- * per SM, at most 1024 threads per SM, 1536 for CDBM_FP32_DF64; each with its own
+ * per SM, at most 1024 threads per SM; each with its own
  * longest-first partition of the tubes) over trial_steps steps, keeps
  * the fastest and reports it.  The state is saved before and restored after the
  * trials, and results do not depend on the tile. */

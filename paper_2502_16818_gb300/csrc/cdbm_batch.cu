@@ -35,10 +35,12 @@ struct TubeInfo {
     int cls;                          // index of the tube's I in BatchArgs::cls
     double lx[2][4];                  // per stage: gamma dt c_g / dx_t
     float lx_f[2][4];
+    float2 lx_f2[2][4];               // lx_f twice (two-column df64 stage)
     double sF[2][4];                  // per stage: gamma h F_g (FP32-bulk reference)
     double Fg[4];                     // reference equilibrium per group
     double rhoF, EF;                  // its conserved moments
     DFShift dfs[2];                   // per stage: the same in df64 (CDBM_FP32_DF64)
+    DFShiftT<float2> dfs2[2];         // dfs with each value twice
 };
 
 struct ClassConsts {
@@ -47,12 +49,15 @@ struct ClassConsts {
     ModelConsts m;
     DFBlocks dfeq[2];                 // eq[] and m in df64 (CDBM_FP32_DF64)
     DFModel dfm;
+    DFBlocksT<float2> dfeq2[2];       // the same with each value twice
+    DFModelT<float2> dfm2;
 };
 
 struct BatchArgs {
     ClassConsts cls[kMaxClasses];
     double a_self[2], a_base[2];
     float a_self_f[2], a_base_f[2];
+    float2 a_self_f2[2], a_base_f2[2];
     long long P;                      // total cells: stride between velocity planes
 };
 
@@ -113,12 +118,59 @@ __device__ __forceinline__ void tube_stage(const TS *g, const TS *base, TS *out,
     }
 }
 
-// Register budget: 384 resident threads per SM for the double-precision equilibrium
-// (168 registers at 128 threads), 768 for the df64 one, whose float arithmetic fits
-// in 80 registers and gains from the extra warps as the single-grid stages do.
-constexpr int batch_min_blocks(int threads, bool df)
+// The df64 stage of one tube with two cells per thread: each thread takes the
+// pairs (x, x + 1) of the tube (x even; x + 1 = x for an odd last cell, computed
+// twice and stored once) and applies every operation of tube_stage<float, kStage,
+// true> to both with the packed FP32x2 instructions, so each cell gets the bits of
+// the one-cell form with about half the instruction issues.
+template <int kStage>
+__device__ __forceinline__ void tube_stage2(const float *g, const float *base, float *out, long long P,
+                                            const TubeInfo &t, const ClassConsts &C, float2 a_self,
+                                            float2 a_base, unsigned *flag)
 {
-    return (df ? 768 : 384) / threads > 0 ? (df ? 768 : 384) / threads : 1;
+    constexpr bool kBase = kStage == 1;
+    const int nx = t.nx;
+    const float2 *lx = t.lx_f2[kStage];
+    const float2 half2 = make_float2(0.5f, 0.5f);
+    for (int x = 2 * threadIdx.x; x < nx; x += 2 * blockDim.x) {
+        const bool two = x + 1 < nx;
+        const int xb = two ? x + 1 : x;
+        const int m2a = x >= 2 ? x - 2 : 0, m1a = x >= 1 ? x - 1 : 0;
+        const int p1a = x + 1 < nx ? x + 1 : nx - 1, p2a = x + 2 < nx ? x + 2 : nx - 1;
+        const int m2b = xb >= 2 ? xb - 2 : 0, m1b = xb >= 1 ? xb - 1 : 0;
+        const int p1b = xb + 1 < nx ? xb + 1 : nx - 1, p2b = xb + 2 < nx ? xb + 2 : nx - 1;
+        float2 fs[kNV], heq[kNV];
+#pragma unroll
+        for (int i = 0; i < kNV; ++i) fs[i] = make_float2(g[i * P + x], g[i * P + xb]);
+        df_equilibrium(C.dfeq2[kStage], C.dfm2, t.dfs2[kStage], fs, heq, flag);
+#pragma unroll
+        for (int i = 0; i < kNV; ++i) {
+            float2 o = fma_rn(a_self, fs[i], heq[i]);
+            if (kBase) o = fma_rn(a_base, make_float2(base[i * P + x], base[i * P + xb]), o);
+            if (dirx(i) != 0) {
+                const float *gp = g + i * P;
+                const bool pos = dirx(i) > 0;
+                const float2 u2 = pos ? make_float2(gp[m2a], gp[m2b]) : make_float2(gp[p2a], gp[p2b]);
+                const float2 u1 = pos ? make_float2(gp[m1a], gp[m1b]) : make_float2(gp[p1a], gp[p1b]);
+                const float2 d1 = pos ? make_float2(gp[p1a], gp[p1b]) : make_float2(gp[m1a], gp[m1b]);
+                const float2 av = sub_rn(fs[i], u1);
+                const float2 bv = sub_rn(d1, fs[i]);
+                const float2 ev = sub_rn(u1, u2);
+                const float2 tt = sub_rn(minmod(bv, av), minmod(av, ev));
+                o = fma_rn(neg(lx[i >> 2]), fma_rn(half2, tt, av), o);
+            }
+            out[i * P + x] = o.x;
+            if (two) out[i * P + xb] = o.y;
+        }
+    }
+}
+
+// Register budget: 384 resident threads per SM for the double-precision equilibrium
+// (168 registers at 128 threads) and for the two-column df64 one, whose two cells
+// of float arithmetic take about as many.
+constexpr int batch_min_blocks(int threads, bool)
+{
+    return 384 / threads > 0 ? 384 / threads : 1;
 }
 
 template <typename TS, int kThreads, bool kDF>
@@ -134,9 +186,15 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks(kThreads, kDF)) bat
         TS *ft = f + t.offset;
         TS *f1t = f1 + t.offset;
         for (int s = 0; s < nsteps; ++s) {
-            tube_stage<TS, 0, kDF>(ft, nullptr, f1t, a.P, t, C, as0, ab0, flag);
-            __syncthreads();
-            tube_stage<TS, 1, kDF>(f1t, ft, ft, a.P, t, C, as1, ab1, flag);
+            if constexpr (kDF) {
+                tube_stage2<0>(ft, nullptr, f1t, a.P, t, C, a.a_self_f2[0], a.a_base_f2[0], flag);
+                __syncthreads();
+                tube_stage2<1>(f1t, ft, ft, a.P, t, C, a.a_self_f2[1], a.a_base_f2[1], flag);
+            } else {
+                tube_stage<TS, 0, kDF>(ft, nullptr, f1t, a.P, t, C, as0, ab0, flag);
+                __syncthreads();
+                tube_stage<TS, 1, kDF>(f1t, ft, ft, a.P, t, C, as1, ab1, flag);
+            }
             __syncthreads();
         }
     }
@@ -453,6 +511,8 @@ cdbm_status cdbm_batch_create(int ntubes, const int *nx, const double *dx, const
         b->args.a_base[s] = alpha[s];
         b->args.a_self_f[s] = (float)b->args.a_self[s];
         b->args.a_base_f[s] = (float)b->args.a_base[s];
+        b->args.a_self_f2[s] = make_float2(b->args.a_self_f[s], b->args.a_self_f[s]);
+        b->args.a_base_f2[s] = make_float2(b->args.a_base_f[s], b->args.a_base_f[s]);
     }
     for (int t = 0; t < ntubes; ++t) {
         if (nx[t] < 1 || !(std::isfinite(dx[t]) && dx[t] > 0) || !(std::isfinite(I[t]) && I[t] >= 0)) {
@@ -483,8 +543,10 @@ cdbm_status cdbm_batch_create(int ntubes, const int *nx, const double *dx, const
             for (int s = 0; s < 2; ++s) {
                 C.eq[s] = scaled(C.unit, gamma[s] * h);
                 C.dfeq[s] = df_blocks(C.eq[s]);
+                C.dfeq2[s] = df_blocks_twice(C.dfeq[s]);
             }
             C.dfm = df_model(C.m);
+            C.dfm2 = df_model_twice(C.dfm);
         }
         TubeInfo &ti = b->info[t];
         memset(&ti, 0, sizeof(ti));
@@ -495,6 +557,7 @@ cdbm_status cdbm_batch_create(int ntubes, const int *nx, const double *dx, const
             for (int g = 0; g < 4; ++g) {
                 ti.lx[s][g] = gamma[s] * dt * vset->v[g] / dx[t];
                 ti.lx_f[s][g] = (float)ti.lx[s][g];
+                ti.lx_f2[s][g] = make_float2(ti.lx_f[s][g], ti.lx_f[s][g]);
             }
         b->offs[t + 1] = b->offs[t] + nx[t];
     }
@@ -584,6 +647,7 @@ cdbm_status cdbm_batch_init(cdbm_batch *b, const double *rho, const double *ux, 
         for (int s = 0; s < 2; ++s) {
             for (int g = 0; g < 4; ++g) ti.sF[s][g] = gamma[s] * h * ti.Fg[g];
             ti.dfs[s] = df_shift(ti.sF[s], ti.rhoF, ti.EF);
+            ti.dfs2[s] = df_shift_twice(ti.dfs[s]);
         }
     }
     const unsigned nb = cells_grid(b->P);
@@ -630,7 +694,7 @@ cdbm_status cdbm_batch_autotune(cdbm_batch *b, int trial_steps, int *threads_out
     cudaEventCreate(&e1);
     const int cand_threads[3] = {64, 128, 256};
     const int cand_bpsm[5] = {1, 2, 3, 4, 6};
-    const int max_threads = b->precision == CDBM_FP32_DF64 ? 1536 : 1024;
+    const int max_threads = 1024;
     float best = 1e30f;
     int bt = b->threads, bb = 3;
     cdbm_status st = CDBM_OK;

@@ -202,5 +202,9 @@ DFModel df_model(const ModelConsts &m);
 DFShift df_shift(const double sF[4], double rhoF, double EF);
 // Fills a.d from the double constants of a.
 void fill_df_consts(StageArgs &a);
+// The same constants with each value twice, for the two-column (packed FP32x2) kernels.
+DFBlocksT<float2> df_blocks_twice(const DFBlocks &d);
+DFModelT<float2> df_model_twice(const DFModel &d);
+DFShiftT<float2> df_shift_twice(const DFShift &d);
 
 }  // namespace cdbm

@@ -764,29 +764,49 @@ void twice_all(const DFPair (&in)[N], DFv<float2> (&out)[N])
 
 }  // namespace
 
+DFBlocksT<float2> df_blocks_twice(const DFBlocks &d)
+{
+    DFBlocksT<float2> t;
+    twice_all(d.S, t.S);
+    twice_all(d.B1, t.B1);
+    twice_all(d.B2, t.B2);
+    twice_all(d.V0, t.V0);
+    twice_all(d.V3, t.V3);
+    twice_all(d.Vs, t.Vs);
+    twice_all(d.Vd, t.Vd);
+    return t;
+}
+
+DFModelT<float2> df_model_twice(const DFModel &d)
+{
+    DFModelT<float2> t;
+    twice_all(d.c, t.c);
+    twice_all(d.w, t.w);
+    t.invK = twice(d.invK);
+    t.Kp4 = twice(d.Kp4);
+    t.Kp6 = twice(d.Kp6);
+    t.twoKp2 = twice(d.twoKp2);
+    return t;
+}
+
+DFShiftT<float2> df_shift_twice(const DFShift &d)
+{
+    DFShiftT<float2> t;
+    twice_all(d.sF, t.sF);
+    t.rhoF = twice(d.rhoF);
+    t.EF = twice(d.EF);
+    return t;
+}
+
 void fill_df_consts(StageArgs &a)
 {
     a.d.b = df_blocks(a.eq);
     a.d.m = df_model(a.m);
     a.d.r = df_shift(a.sF, a.rhoF, a.EF);
     // each value twice for the two-column kernel
-    DFConstsT<float2> &t = a.d2;
-    twice_all(a.d.b.S, t.b.S);
-    twice_all(a.d.b.B1, t.b.B1);
-    twice_all(a.d.b.B2, t.b.B2);
-    twice_all(a.d.b.V0, t.b.V0);
-    twice_all(a.d.b.V3, t.b.V3);
-    twice_all(a.d.b.Vs, t.b.Vs);
-    twice_all(a.d.b.Vd, t.b.Vd);
-    twice_all(a.d.m.c, t.m.c);
-    twice_all(a.d.m.w, t.m.w);
-    t.m.invK = twice(a.d.m.invK);
-    t.m.Kp4 = twice(a.d.m.Kp4);
-    t.m.Kp6 = twice(a.d.m.Kp6);
-    t.m.twoKp2 = twice(a.d.m.twoKp2);
-    twice_all(a.d.r.sF, t.r.sF);
-    t.r.rhoF = twice(a.d.r.rhoF);
-    t.r.EF = twice(a.d.r.EF);
+    a.d2.b = df_blocks_twice(a.d.b);
+    a.d2.m = df_model_twice(a.d.m);
+    a.d2.r = df_shift_twice(a.d.r);
     a.a_base_f2 = make_float2(a.a_base_f, a.a_base_f);
     a.a_self_f2 = make_float2(a.a_self_f, a.a_self_f);
     for (int g = 0; g < 4; ++g) {
