@@ -293,8 +293,19 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_stage_kernel(const double
 #pragma unroll
         for (int i = 0; i < kNV; ++i) {
             const int grp = i >> 2;
-            double gb = fma(a.a_self, o[i], mb[i]);
             const double *gp = g + i * P, *op = ob + i * P;
+            if constexpr (kMode == CDBM_ADJ_LIMITER_FROZEN) {
+                // l (o_{m+s} - o_m) per direction, with the -l o_m terms in the self factor
+                const double self = dirx(i) == 0 ? a.a_self_y[grp] : (diry(i) == 0 ? a.a_self_x[grp]
+                                                                                    : a.a_self_xy[grp]);
+                double gb = fma(self, o[i], mb[i]);
+                if (dirx(i) != 0) gb = fma(a.lx[grp], op[row + xs[2 + dirx(i)]], gb);
+                if (diry(i) != 0 && ny > 1) gb = fma(a.ly[grp], op[(size_t)ys[2 + diry(i)] * nx + x], gb);
+                if (prev) gb = fma(c_prev, prev[i * P + c], gb);
+                out_bar[i * P + c] = gb;
+                continue;
+            }
+            double gb = fma(a.a_self, o[i], mb[i]);
             if (dirx(i) != 0) {
                 const int s = dirx(i);
                 // upwind order: index of m + k s

@@ -334,6 +334,12 @@ void build_stages(cdbm_ctx *c)
             a.lx[g] = r.gamma * c->dt * c->mc.c[g] / c->grid.dx;
             a.ly[g] = r.gamma * c->dt * c->mc.c[g] / c->grid.dy;
         }
+        for (int g = 0; g < 4; ++g) {
+            const double ly = c->grid.ny > 1 ? a.ly[g] : 0.0;
+            a.a_self_x[g] = a.a_self - a.lx[g];
+            a.a_self_y[g] = a.a_self - ly;
+            a.a_self_xy[g] = a.a_self - a.lx[g] - ly;
+        }
         a.a_base_f = (float)a.a_base;
         a.a_self_f = (float)a.a_self;
         for (int g = 0; g < 4; ++g) {

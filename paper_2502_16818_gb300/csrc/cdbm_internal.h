@@ -105,6 +105,11 @@ struct StageArgs {
     // cancel because alpha + beta = 1 in every stage.
     double sF[4];
     double rhoF, EF;
+    // a_self minus the transport coefficients of a velocity's directions, per group:
+    // x only (E, W), y only (N, S; a_self when ny = 1), both (diagonals; x only when
+    // ny = 1).  The frozen-limiter adjoint stage uses them to fold -l o_m into the
+    // self term.
+    double a_self_x[4], a_self_y[4], a_self_xy[4];
     DFConsts d;                   // df64 copies (CDBM_FP32_DF64)
     DFConstsT<float2> d2;         // the same, each value twice (two-column kernel)
     float2 a_base_f2, a_self_f2;  // a_base_f, a_self_f, lx_f, ly_f twice
