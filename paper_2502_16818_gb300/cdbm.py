@@ -25,8 +25,8 @@ CDBM_ADJ_LIMITER_EXACT, CDBM_ADJ_LIMITER_FROZEN_RATIO, CDBM_ADJ_LIMITER_FROZEN =
 CDBM_RK2_TVD, CDBM_RK2_MIDPOINT = 0, 1
 
 #: every entry point declared in include/cdbm.h
-EXPORTS = ("cdbm_create", "cdbm_set_rk", "cdbm_init", "cdbm_step", "cdbm_set_small_grid_path", "cdbm_set_row_marching", "cdbm_macros",
-           "cdbm_tne", "cdbm_conserved_sums", "cdbm_get_state", "cdbm_set_state", "cdbm_state_ptr", "cdbm_time",
+EXPORTS = ("cdbm_create", "cdbm_set_rk", "cdbm_init", "cdbm_step", "cdbm_set_small_grid_path",
+           "cdbm_set_row_marching", "cdbm_macros", "cdbm_tne", "cdbm_conserved_sums", "cdbm_get_state", "cdbm_set_state", "cdbm_state_ptr", "cdbm_time",
            "cdbm_sync", "cdbm_last_error", "cdbm_destroy", "cdbm_step_noalloc",
            "cdbm_batch_create", "cdbm_batch_init", "cdbm_batch_step", "cdbm_batch_autotune",
            "cdbm_batch_set_tile", "cdbm_batch_macros", "cdbm_batch_info", "cdbm_batch_sync",

@@ -494,3 +494,34 @@ def test_row_marching_matches_one_cell_per_thread(prec, shape, bc):
         states.append(s.state().cpu().numpy())
         s.close()
     assert np.array_equal(states[0], states[1]), (prec, shape, bc)
+
+
+def test_misaligned_allocator_block_is_refused():
+    """The kernels move 8- and 16-byte words, so the context allocator must return
+    16-byte aligned blocks: a block that is not is handed back to free and
+    cdbm_create fails with CDBM_ENOMEM before anything runs on it."""
+    import ctypes
+    from paper_2502_16818_gb300 import cdbm
+    dev = torch.cuda.current_device()
+    held, freed = {}, []
+
+    def _alloc(nbytes, strm, user):
+        p = torch.cuda.caching_allocator_alloc(int(nbytes) + 64, dev, strm or 0)
+        held[p + 4] = p
+        return p + 4
+
+    def _free(ptr, nbytes, strm, user):
+        freed.append(ptr)
+        torch.cuda.caching_allocator_delete(held.pop(ptr))
+
+    a_cb, f_cb = cdbm.ALLOC_FN(_alloc), cdbm.FREE_FN(_free)
+    alloc = cdbm.cdbm_allocator(a_cb, f_cb, None)
+    grid = cdbm.cdbm_grid(64, 8, 1.0 / 64, 1.0 / 64, cdbm.CDBM_BC_PERIODIC, cdbm.CDBM_BC_PERIODIC)
+    vg, eg = W.VSET_SOUND
+    vset = cdbm.cdbm_vset((ctypes.c_double * 4)(*vg), (ctypes.c_double * 4)(*eg))
+    with pytest.raises(cdbm.CdbmError) as e:
+        cdbm.cdbm_create(grid, vset, 1.0, 1e-3, 1e-4, cdbm.CDBM_FP32_DF64, torch.cuda.current_stream().cuda_stream,
+                         alloc)
+    torch.cuda.synchronize()
+    assert e.value.status == cdbm.CDBM_ENOMEM
+    assert freed and not held
