@@ -391,7 +391,7 @@ cdbm_status build_graph(cdbm_ctx *c)
             p.func = c->launch[k].func;
             p.gridDim = c->launch[k].grid;
             p.blockDim = c->launch[k].block;
-            p.sharedMemBytes = 0;
+            p.sharedMemBytes = (unsigned)c->launch[k].smem;
             p.kernelParams = args;
             cudaGraphNode_t node;
             cudaError_t e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &p);

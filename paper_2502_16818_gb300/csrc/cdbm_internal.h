@@ -165,6 +165,7 @@ cudaError_t launch_field_means(const double *rho, const double *T, size_t n, dou
 struct StageLaunch {
     void *func;
     dim3 grid, block;
+    size_t smem = 0;              // dynamic shared memory bytes
 };
 // allow_march = false keeps 2-D grids on the one-cell-per-thread stage kernel.
 StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count, int prec,

@@ -296,7 +296,28 @@ __global__ void __launch_bounds__(kStageThreads, stage_min_blocks(kDF))
 // bits of the one-column kernel, with about half the instruction issues for the
 // arithmetic, which bounds that kernel.  kVec: nx is even, so the pair (x0, x1) of a
 // row is 8-byte aligned and moves as one float2.
+// The rows a thread needs next are copied ahead into shared memory with cp.async
+// (no registers held while they are in flight): at row y the thread stages row y+1,
+// which its y transport reads after the equilibrium and which is the state of the
+// next row.  Each thread copies and reads only its own two columns, so the copies
+// need the thread's own wait only, no block barrier.
 constexpr int kMarch2MinBlocks = 3;
+// Rows staged ahead by cp.async: two buffers of [kNV][kStageThreads] float2.
+constexpr size_t kMarch2StageBytes = 2 * kNV * kStageThreads * sizeof(float2);
+
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <bool kBase, bool kVec>
 __global__ void __launch_bounds__(kStageThreads, kMarch2MinBlocks)
@@ -305,6 +326,7 @@ __global__ void __launch_bounds__(kStageThreads, kMarch2MinBlocks)
 {
     __shared__ float2 carry_u[kNY][kStageThreads];
     __shared__ float2 carry_n[kNY][kStageThreads];
+    extern __shared__ __align__(16) float2 staged[];  // [2][kNV][kStageThreads]
     const int nx = a.nx, ny = a.ny;
     const int tid = threadIdx.x;
     const int x0 = 2 * (int)(blockIdx.x * blockDim.x + tid);
@@ -327,6 +349,21 @@ __global__ void __launch_bounds__(kStageThreads, kMarch2MinBlocks)
         else return make_float2(__ldg(p + x0), __ldg(p + x1));
     };
     auto ld_at = [&](const float *p, int ca, int cb) -> float2 { return make_float2(__ldg(p + ca), __ldg(p + cb)); };
+    auto stage_row = [&](int b, size_t row) {       // the thread's two cells of a row, all planes
+#pragma unroll
+        for (int i = 0; i < kNV; ++i) {
+            float2 *dst = staged + (b * kNV + i) * kStageThreads + tid;
+            const float *src = g + i * P + row;
+            if constexpr (kVec) {
+                cp_async8(dst, src + x0);
+            } else {
+                cp_async4(&dst->x, src + x0);
+                cp_async4(&dst->y, src + x1);
+            }
+        }
+        cp_async_commit();
+    };
+    auto staged_at = [&](int b, int i) -> float2 { return staged[(b * kNV + i) * kStageThreads + tid]; };
 
     // prologue: U_{y0} and N_{y0 - 1} for s = +1, N_{y0} for s = -1
     {
@@ -353,11 +390,16 @@ __global__ void __launch_bounds__(kStageThreads, kMarch2MinBlocks)
         }
     }
 
-    for (int y = y0; y < y1; ++y) {
+    stage_row(0, (size_t)y0 * nx);
+    for (int y = y0, b = 0; y < y1; ++y, b ^= 1) {
         const size_t row = (size_t)y * nx;
+        const size_t rp1 = (size_t)neighbour(y + 1, ny, a.bc_y) * nx;
+        const size_t rp2 = (size_t)neighbour(y + 2, ny, a.bc_y) * nx;
+        stage_row(b ^ 1, rp1);                        // row y+1 while this one computes
+        cp_async_wait<1>();                           // row y, staged one row earlier
         float2 fs[kNV], o[kNV], heq[kNV];
 #pragma unroll
-        for (int i = 0; i < kNV; ++i) fs[i] = ld(g + i * P + row);
+        for (int i = 0; i < kNV; ++i) fs[i] = staged_at(b, i);
         df_equilibrium(a.d2.b, a.d2.m, a.d2.r, fs, heq, flag);
 #pragma unroll
         for (int i = 0; i < kNV; ++i) {
@@ -376,8 +418,7 @@ __global__ void __launch_bounds__(kStageThreads, kMarch2MinBlocks)
                 o[i] = fma_rn(neg(a.lx_f2[i >> 2]), fma_rn(half2, t, av), o[i]);
             }
         }
-        const size_t rp1 = (size_t)neighbour(y + 1, ny, a.bc_y) * nx;
-        const size_t rp2 = (size_t)neighbour(y + 2, ny, a.bc_y) * nx;
+        cp_async_wait<0>();                           // row y+1
 #pragma unroll
         for (int k = 0; k < kNY; ++k) {
             const int i = yvel(k);
@@ -386,13 +427,13 @@ __global__ void __launch_bounds__(kStageThreads, kMarch2MinBlocks)
             const float2 n = carry_n[k][tid];
             float2 t;
             if (diry(i) > 0) {
-                const float2 un = sub_rn(ld(gp + rp1), fs[i]);              // U_{y+1}
+                const float2 un = sub_rn(staged_at(b ^ 1, i), fs[i]);       // U_{y+1}
                 const float2 nn = minmod(un, u);                            // N_y
                 t = sub_rn(nn, n);
                 carry_u[k][tid] = un;
                 carry_n[k][tid] = nn;
             } else {
-                const float2 un = sub_rn(ld(gp + rp1), ld(gp + rp2));       // U_{y+1}
+                const float2 un = sub_rn(staged_at(b ^ 1, i), ld(gp + rp2)); // U_{y+1}
                 const float2 nn = minmod(u, un);                            // N_{y+1}
                 t = sub_rn(n, nn);
                 carry_u[k][tid] = un;
@@ -697,6 +738,13 @@ StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count
         L.func = pair ? stage_march2_func(with_base, (a.nx & 1) == 0)
                  : prec == CDBM_FP32_BULK ? stage_func<float, false>(true, with_base, false)
                                           : stage_func<double, false>(true, with_base, false);
+        if (pair) {
+            // rows staged by cp.async: dynamic shared memory beside the static carries
+            L.smem = kMarch2StageBytes;
+            if (cudaFuncSetAttribute(L.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem) !=
+                cudaSuccess)
+                cudaGetLastError();   // the launch then reports the error
+        }
         L.block = dim3(kStageThreads, 1, 1);
         const unsigned yblocks = (unsigned)((a.ny + R - 1) / R);
         L.grid = dim3(xblocks, yblocks < 65535 ? yblocks : 65535, 1);
@@ -819,7 +867,7 @@ cudaError_t launch_stage(const StageLaunch &L, const void *g, const void *base, 
                          const StageArgs &a, unsigned *flag, cudaStream_t s)
 {
     void *args[] = {(void *)&g, (void *)&base, (void *)&out, (void *)&a, (void *)&flag};
-    return cudaLaunchKernel(L.func, L.grid, L.block, args, 0, s);
+    return cudaLaunchKernel(L.func, L.grid, L.block, args, L.smem, s);
 }
 
 }  // namespace cdbm
