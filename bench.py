@@ -48,8 +48,8 @@ FP64_LANES_PER_CLK_PER_SM = 2       # 1.25 TFLOP/s nominal FP64 / (2 flops x 152
 # DRAM traffic of one stage launch (mean of the two stages) from one ncu capture of
 # the stage kernels; valid only while the kernel sources hash to TRAFFIC_SHA.
 # Captured at 1024^2 (134 MB per plane set, above L2) and scaled by 16 cells-fold.
-TRAFFIC_SHA = "1f26325bd3aa5815"
-TRAFFIC_BYTES_PER_LAUNCH = 5.103e9
+TRAFFIC_SHA = "534ca589fdc82f23"
+TRAFFIC_BYTES_PER_LAUNCH = 5.108e9
 
 
 STAGE_SOURCES = ("cdbm_device.cuh", "cdbm_kernels.cu", "cdbm_internal.h")
