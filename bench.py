@@ -21,6 +21,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -46,22 +47,31 @@ BYTES_PER_CELL_STEP = 640
 FP64_LANES_PER_CLK_PER_SM = 2       # 1.25 TFLOP/s nominal FP64 / (2 flops x 152 SMs x 2.07 GHz)
 
 # DRAM traffic of one stage launch (mean of the two stages) from one ncu capture of
-# the stage kernels; valid only while the kernel sources hash to TRAFFIC_SHA.
+# the stage kernels; valid only while the code of the kernel sources (comments
+# stripped) hashes to TRAFFIC_SHA.
 # Captured at 1024^2 (134 MB per plane set, above L2) and scaled by 16 cells-fold.
-TRAFFIC_SHA = "534ca589fdc82f23"
+TRAFFIC_SHA = "e0e2bc630747b544"
 TRAFFIC_BYTES_PER_LAUNCH = 5.108e9
 
 
 STAGE_SOURCES = ("cdbm_device.cuh", "cdbm_kernels.cu", "cdbm_internal.h")
 
 
+def _code_only(text):
+    """C/C++ source without comments and blank lines (string literals in these
+    files hold no comment markers)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*", "", line).rstrip() for line in text.splitlines())
+    return "\n".join(line for line in lines if line)
+
+
 def kernel_sha():
-    """Hash of the sources that define the stage kernels."""
+    """Hash of the code (comments stripped) of the sources that define the stage kernels."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2502_16818_gb300", "csrc")
     for name in STAGE_SOURCES:
-        with open(os.path.join(csrc, name), "rb") as fh:
-            h.update(name.encode() + fh.read())
+        with open(os.path.join(csrc, name), encoding="utf-8") as fh:
+            h.update(name.encode() + _code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

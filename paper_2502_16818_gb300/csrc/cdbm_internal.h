@@ -142,8 +142,9 @@ constexpr size_t kThreadErrorBytes = 256;
 char *thread_error_buffer();
 
 // ---- launchers (cdbm_kernels.cu); each returns the launch error ----
-// `prec` is the storage precision of the distribution buffers (CDBM_FP64 or
-// CDBM_FP32_BULK); fields, Delta* and sums are always double.
+// `prec` is the precision mode (CDBM_FP64, CDBM_FP32_BULK or CDBM_FP32_DF64), which
+// sets the storage of the distribution buffers; fields, Delta* and sums are always
+// double.
 cudaError_t launch_init(const FieldArgs &a, const double *rho, const double *ux,
                         const double *uy, const double *T, void *f, int prec, unsigned *flag,
                         cudaStream_t s);

@@ -5,10 +5,12 @@
 // equilibrium of a stage are computed in double, or in double-float arithmetic
 // on the FP32 pipe for CDBM_FP32_DF64 (template flag kDF).
 //
-// Layout: f[16][ny][nx] (velocity plane outermost, x fastest).  One thread owns
-// one cell; a block covers a run of cells along x of one row, so centre loads
-// and stores of a warp are coalesced rows and the stencil neighbours
-// (x +- 1, 2 and the rows y +- 1, 2) are served from L1/L2.
+// Layout: f[16][ny][nx] (velocity plane outermost, x fastest).  A block covers a
+// run of columns along x, so centre loads and stores of a warp are coalesced rows
+// and the stencil neighbours (x +- 1, 2 and the rows y +- 1, 2) are served from
+// L1/L2 or shared memory.  stage_kernel gives each thread one cell; the
+// row-marching kernels give each thread one column (two for the df64 state) over a
+// run of rows.
 #include "cdbm_stage.cuh"
 
 namespace cdbm {
