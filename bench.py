@@ -151,6 +151,16 @@ def workload(n):
     return W.taylor_green(n=n, I=3.0)
 
 
+def arm_config(a, w, world):
+    """The config of the bench line, the same for both arms."""
+    plane_set_bytes = 16 * 8 * w.nx * w.ny
+    return {"workload": "taylor_green_%dx%d_fp64" % (a.n, a.n), "nx": w.nx, "ny": w.ny,
+            "I": w.I, "tau": w.tau, "dt": w.dt, "vset": [w.vg, w.eg], "precision": "fp64",
+            "rk": "tvd2",
+            "l2": "state %.3g GB per buffer vs 129 MB L2, no flush" % (plane_set_bytes / 1e9),
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def cpu_sample(w, side):
     """A side x side block of the workload's initial fields (zero-gradient edges)."""
     import oracle
@@ -209,7 +219,7 @@ def run_reference(a, rank, world):
         return
     w = workload(a.n)
     import oracle
-    side = 512
+    side = min(512, w.nx)
     m, sub = cpu_sample(w, side)
     f = oracle.init(m, *sub)
     for _ in range(a.warmup):
@@ -224,7 +234,7 @@ def run_reference(a, rank, world):
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3 / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "taylor_green_%dx%d_fp64" % (a.n, a.n), "sample": "%dx%d" % (side, side)},
+        "config": arm_config(a, w, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": m.threads, "kind": "oracle",
                          "sample": "%dx%d block of the %d^2 Taylor-Green initial state, one RK2 step "
                                    "per bench step" % (side, side, a.n)},
@@ -316,11 +326,7 @@ def run_cdbm(a, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "taylor_green_%dx%d_fp64" % (a.n, a.n), "nx": w.nx, "ny": w.ny,
-                   "I": w.I, "tau": w.tau, "dt": w.dt, "vset": [w.vg, w.eg], "precision": "fp64",
-                   "rk": "tvd2",
-                   "l2": "state %.3g GB per buffer vs 129 MB L2, no flush" % (plane_set_bytes / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": arm_config(a, w, world),
         "gpu_launches": 2 * a.steps,
         "clocks": clocks,
         "roofline": roofline,
