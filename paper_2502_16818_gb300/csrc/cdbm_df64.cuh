@@ -160,6 +160,92 @@ __device__ __forceinline__ void rebuild_diag_f(L *o, L s0, L q, L sx, L sy)
     o[3] = add_rn(Q, V);
 }
 
+// The df64 equilibrium in three parts, so that a cell can also be split over four
+// threads, one per velocity group (the cluster kernel for small FP64-free grids):
+// the group components (s0, sx, sy) of one group's four stored deviations; the
+// scalars every group needs (moments, primitives, raw-moment factors); and one
+// group's four equilibrium values.  df_equilibrium() is the three in sequence.
+
+// Group components of group g from its four stored deviations q (the operations of
+// conserved() on df64 values).
+template <typename L>
+__device__ __forceinline__ void df_group_components(int g, const L q[4], dfl<L> &s0, dfl<L> &sx, dfl<L> &sy)
+{
+    if ((g & 1) == 0) {
+        s0 = df_add(two_sum(q[0], q[2]), two_sum(q[1], q[3]));
+        sx = two_sum(q[0], neg(q[2]));
+        sy = two_sum(q[1], neg(q[3]));
+    } else {
+        const dfl<L> e = two_sum(q[0], q[3]), w = two_sum(q[1], q[2]);
+        sx = df_sub(e, w);
+        sy = df_sub(two_sum(q[0], q[1]), two_sum(q[2], q[3]));
+        s0 = df_add(e, w);
+    }
+}
+
+template <typename L>
+struct DFScalars {
+    dfl<L> rho, E, jx, jy, r, ux, uy, jyuy, ru2, P, T, u2, du2, m1416, W4, d57, m6;
+};
+
+// Moments, primitives and raw-moment factors from the group components of all four
+// groups (the steps of primitives() and the shared part of equilibrium<true>()).
+template <typename L>
+__device__ __forceinline__ DFScalars<L> df_scalars(const DFModelT<L> &d, const DFShiftT<L> &R, const dfl<L> s0[4],
+                                                   const dfl<L> sx[4], const dfl<L> sy[4], unsigned *flag)
+{
+    DFScalars<L> c;
+    c.rho = df_add(df_add(df_add(s0[0], s0[1]), df_add(s0[2], s0[3])), R.rhoF);
+    c.jx = df_mul(d.c[0], sx[0]);
+    c.jy = df_mul(d.c[0], sy[0]);
+    c.E = df_add(df_mul(d.w[0], s0[0]), R.EF);
+#pragma unroll
+    for (int g = 1; g < 4; ++g) {
+        c.jx = df_fma(d.c[g], sx[g], c.jx);
+        c.jy = df_fma(d.c[g], sy[g], c.jy);
+        c.E = df_fma(d.w[g], s0[g], c.E);
+    }
+    c.r = df_rcp(c.rho);
+    c.ux = df_mul(c.jx, c.r);
+    c.uy = df_mul(c.jy, c.r);
+    c.jyuy = df_mul(c.jy, c.uy);
+    c.ru2 = df_fma(c.jx, c.ux, c.jyuy);
+    c.P = df_mul(df_sub(c.E, c.ru2), d.invK);
+    c.T = df_mul(c.P, c.r);
+    if (flag && !(positive_finite_f(c.rho.hi) && positive_finite_f(c.P.hi))) atomicOr(flag, kFlagNonPhys);
+    const dfl<L> ux2 = df_mul(c.ux, c.ux), uy2 = df_mul(c.uy, c.uy);
+    c.u2 = df_add(ux2, uy2);
+    c.du2 = df_sub(ux2, uy2);
+    c.m1416 = df_fma(c.T, df_fma(d.Kp6, c.ru2, df_mul(d.twoKp2, c.P)), df_mul(c.ru2, c.u2));
+    c.W4 = df_fma(d.Kp4, c.T, c.u2);
+    c.d57 = df_sub(df_mul(c.jx, c.ux), c.jyuy);
+    c.m6 = df_mul(c.jx, c.uy);
+    return c;
+}
+
+// The four scaled equilibrium deviations of group g.
+template <typename L>
+__device__ __forceinline__ void df_group_equilibrium(int g, const DFBlocksT<L> &B, const DFShiftT<L> &R,
+                                                     const DFScalars<L> &c, L heq[4])
+{
+    const dfl<L> *S = B.S + 4 * g;
+    const dfl<L> s = df_fma(S[3], c.m1416, df_fma(S[2], c.ru2, df_fma(S[1], c.E, df_mul(S[0], c.rho))));
+    const L c0 = df_to_float(df_sub(s, R.sF[g]));
+    // V0 + V1 u_x^2 + V2 u_y^2 + V3 T and its mirror, through the shared part
+    // V0 + V3 T + (V1 + V2)/2 u^2 and the odd part (V1 - V2)/2 (u_x^2 - u_y^2)
+    const dfl<L> cm = df_fma(B.Vs[g], c.u2, df_fma(B.V3[g], c.T, B.V0[g]));
+    const dfl<L> cd = df_mul(B.Vd[g], c.du2);
+    const L cx = df_to_float(df_mul(c.jx, df_add(cm, cd)));
+    const L cy = df_to_float(df_mul(c.jy, df_sub(cm, cd)));
+    if ((g & 1) == 0) {                 // g = 0: a, g = 2: c
+        const L dq = df_to_float(df_mul(c.d57, df_fma(B.B1[g + 1], c.W4, B.B1[g])));
+        rebuild_axis_f(heq, c0, dq, cx, cy);
+    } else {                            // g = 1: b, g = 3: d
+        const L q = df_to_float(df_mul(c.m6, df_fma(B.B2[g], c.W4, B.B2[g - 1])));
+        rebuild_diag_f(heq, c0, q, cx, cy);
+    }
+}
+
 // Scaled equilibrium deviation of one cell (or, with L = float2, of two cells) of
 // the single-precision state, in df64: heq_i = gamma h (f_eq,i(m(F + g)) - F_i)
 // rounded to float, from the stored deviations g (the same steps as primitives()
@@ -170,61 +256,10 @@ __device__ __forceinline__ void df_equilibrium(const DFBlocksT<L> &B, const DFMo
 {
     dfl<L> s0[4], sx[4], sy[4];
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {
-        const L *q = fs + 4 * g;
-        if ((g & 1) == 0) {
-            s0[g] = df_add(two_sum(q[0], q[2]), two_sum(q[1], q[3]));
-            sx[g] = two_sum(q[0], neg(q[2]));
-            sy[g] = two_sum(q[1], neg(q[3]));
-        } else {
-            const dfl<L> e = two_sum(q[0], q[3]), w = two_sum(q[1], q[2]);
-            sx[g] = df_sub(e, w);
-            sy[g] = df_sub(two_sum(q[0], q[1]), two_sum(q[2], q[3]));
-            s0[g] = df_add(e, w);
-        }
-    }
-    const dfl<L> rho = df_add(df_add(df_add(s0[0], s0[1]), df_add(s0[2], s0[3])), R.rhoF);
-    dfl<L> jx = df_mul(d.c[0], sx[0]), jy = df_mul(d.c[0], sy[0]), E = df_add(df_mul(d.w[0], s0[0]), R.EF);
+    for (int g = 0; g < 4; ++g) df_group_components(g, fs + 4 * g, s0[g], sx[g], sy[g]);
+    const DFScalars<L> c = df_scalars(d, R, s0, sx, sy, flag);
 #pragma unroll
-    for (int g = 1; g < 4; ++g) {
-        jx = df_fma(d.c[g], sx[g], jx);
-        jy = df_fma(d.c[g], sy[g], jy);
-        E = df_fma(d.w[g], s0[g], E);
-    }
-    const dfl<L> r = df_rcp(rho);
-    const dfl<L> ux = df_mul(jx, r), uy = df_mul(jy, r);
-    const dfl<L> jyuy = df_mul(jy, uy);
-    const dfl<L> ru2 = df_fma(jx, ux, jyuy);
-    const dfl<L> P = df_mul(df_sub(E, ru2), d.invK);
-    const dfl<L> T = df_mul(P, r);
-    if (!(positive_finite_f(rho.hi) && positive_finite_f(P.hi))) atomicOr(flag, kFlagNonPhys);
-
-    const dfl<L> ux2 = df_mul(ux, ux), uy2 = df_mul(uy, uy), u2 = df_add(ux2, uy2), du2 = df_sub(ux2, uy2);
-    const dfl<L> m1416 = df_fma(T, df_fma(d.Kp6, ru2, df_mul(d.twoKp2, P)), df_mul(ru2, u2));
-    const dfl<L> W4 = df_fma(d.Kp4, T, u2);
-    const dfl<L> d57 = df_sub(df_mul(jx, ux), jyuy);
-    const dfl<L> m6 = df_mul(jx, uy);
-    L c0[4], cx[4], cy[4];
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-        const dfl<L> *S = B.S + 4 * g;
-        const dfl<L> s = df_fma(S[3], m1416, df_fma(S[2], ru2, df_fma(S[1], E, df_mul(S[0], rho))));
-        c0[g] = df_to_float(df_sub(s, R.sF[g]));
-        // V0 + V1 u_x^2 + V2 u_y^2 + V3 T and its mirror, through the shared part
-        // V0 + V3 T + (V1 + V2)/2 u^2 and the odd part (V1 - V2)/2 (u_x^2 - u_y^2)
-        const dfl<L> cm = df_fma(B.Vs[g], u2, df_fma(B.V3[g], T, B.V0[g]));
-        const dfl<L> cd = df_mul(B.Vd[g], du2);
-        cx[g] = df_to_float(df_mul(jx, df_add(cm, cd)));
-        cy[g] = df_to_float(df_mul(jy, df_sub(cm, cd)));
-    }
-    const L dqa = df_to_float(df_mul(d57, df_fma(B.B1[1], W4, B.B1[0])));
-    const L dqc = df_to_float(df_mul(d57, df_fma(B.B1[3], W4, B.B1[2])));
-    const L qb = df_to_float(df_mul(m6, df_fma(B.B2[1], W4, B.B2[0])));
-    const L qd = df_to_float(df_mul(m6, df_fma(B.B2[3], W4, B.B2[2])));
-    rebuild_axis_f(heq + 0, c0[0], dqa, cx[0], cy[0]);
-    rebuild_diag_f(heq + 4, c0[1], qb, cx[1], cy[1]);
-    rebuild_axis_f(heq + 8, c0[2], dqc, cx[2], cy[2]);
-    rebuild_diag_f(heq + 12, c0[3], qd, cx[3], cy[3]);
+    for (int g = 0; g < 4; ++g) df_group_equilibrium(g, B, R, c, heq + 4 * g);
 }
 
 }  // namespace cdbm

@@ -259,12 +259,118 @@ __global__ void __launch_bounds__(256) small1d_split_kernel(double *f, int nstep
     }
 }
 
+// df64 variant with a cell split over two threads: thread h of the pair takes the
+// velocity groups 2h (axis) and 2h + 1 (diagonal), so both threads run the same
+// instruction sequence.  The pair exchanges its group components by warp shuffles,
+// both form the moments, primitives and raw-moment factors (df_scalars, the same
+// operations), and each builds and updates only its own eight velocities.  Every
+// value goes through the operations of the one-thread kernel in the same order, so
+// the result is the same bit for bit; the dependent chain of a stage is about a third
+// shorter, and that chain sets the time of a stage on these grids.
+template <bool kBase>
+__device__ __forceinline__ void split_stage_df(const cg::cluster_group &cl, const float *src, const float *base,
+                                               float *dst, const StageArgs &a, int chunk, int rank, int x0, int len,
+                                               unsigned *flag)
+{
+    const int t = threadIdx.x;
+    const int h = t & 1;                              // groups 2h and 2h + 1 of the cell
+    const int lx0 = t >> 1;
+    const bool live = lx0 < len;
+    const int lx = live ? lx0 : len - 1;              // idle threads mirror the last cell
+    const int gx = x0 + lx;
+    const int nx = a.nx;
+    float q[8], bs[8], up2[8], up1[8], dn1[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        q[j] = src[(8 * h + j) * chunk + lx];
+        bs[j] = kBase ? base[(8 * h + j) * chunk + lx] : 0.0f;
+    }
+    const bool inner = lx >= 2 && lx + 2 < len;
+    const int xm2 = neighbour(gx - 2, nx, a.bc_x), xm1 = neighbour(gx - 1, nx, a.bc_x);
+    const int xp1 = neighbour(gx + 1, nx, a.bc_x), xp2 = neighbour(gx + 2, nx, a.bc_x);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int i = 8 * h + j;
+        const int sx = dirx(j);                       // dirx depends on i mod 8 only
+        if (sx == 0) {
+            up2[j] = up1[j] = dn1[j] = 0.0f;
+        } else if (inner) {
+            const float *p = src + i * chunk + lx;
+            up2[j] = p[sx > 0 ? -2 : 2];
+            up1[j] = p[sx > 0 ? -1 : 1];
+            dn1[j] = p[sx > 0 ? 1 : -1];
+        } else {
+            up2[j] = cluster_value(cl, src, chunk, rank, i, sx > 0 ? xm2 : xp2);
+            up1[j] = cluster_value(cl, src, chunk, rank, i, sx > 0 ? xm1 : xp1);
+            dn1[j] = cluster_value(cl, src, chunk, rank, i, sx > 0 ? xp1 : xm1);
+        }
+    }
+    const DFConsts &D = a.d;
+    df a0, ax, ay, b0, bx, by;                        // own axis group 2h, diagonal group 2h + 1
+    df_group_components(0, q, a0, ax, ay);
+    df_group_components(1, q + 4, b0, bx, by);
+    auto other = [](float v) { return __shfl_xor_sync(0xffffffffu, v, 1); };
+    const df pa0 = {other(a0.hi), other(a0.lo)}, pax = {other(ax.hi), other(ax.lo)}, pay = {other(ay.hi), other(ay.lo)};
+    const df pb0 = {other(b0.hi), other(b0.lo)}, pbx = {other(bx.hi), other(bx.lo)}, pby = {other(by.hi), other(by.lo)};
+    df s0[4], sx4[4], sy4[4];
+    s0[0] = h ? pa0 : a0;   sx4[0] = h ? pax : ax;   sy4[0] = h ? pay : ay;
+    s0[1] = h ? pb0 : b0;   sx4[1] = h ? pbx : bx;   sy4[1] = h ? pby : by;
+    s0[2] = h ? a0 : pa0;   sx4[2] = h ? ax : pax;   sy4[2] = h ? ay : pay;
+    s0[3] = h ? b0 : pb0;   sx4[3] = h ? bx : pbx;   sy4[3] = h ? by : pby;
+    const DFScalars<float> c = df_scalars(D.m, D.r, s0, sx4, sy4, (live && h == 0) ? flag : nullptr);
+    float heq[8];
+    df_group_equilibrium(2 * h, D.b, D.r, c, heq);
+    df_group_equilibrium(2 * h + 1, D.b, D.r, c, heq + 4);
+    float o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        o[j] = fmaf(a.a_self_f, q[j], heq[j]);
+        if (kBase) o[j] = fmaf(a.a_base_f, bs[j], o[j]);
+        if (dirx(j) != 0) o[j] = fmaf(-a.lx_f[2 * h + (j >> 2)], nnd(up2[j], up1[j], q[j], dn1[j]), o[j]);
+    }
+    if (live) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) dst[(8 * h + j) * chunk + lx] = o[j];
+    }
+}
+
+__global__ void __launch_bounds__(256) small1d_split_df_kernel(float *f, int nsteps, const StageArgs a0,
+                                                               const StageArgs a1, unsigned *flag, int chunk)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *s0 = reinterpret_cast<float *>(smem_raw);
+    float *s1 = s0 + kNV * chunk;
+    const cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int nx = a0.nx;
+    const int x0 = rank * chunk;
+    const int len = nx - x0 < chunk ? (nx - x0 > 0 ? nx - x0 : 0) : chunk;
+    for (int k = threadIdx.x; k < kNV * len; k += blockDim.x) {
+        const int i = k / len, lx = k - i * len;
+        s0[i * chunk + lx] = f[(size_t)i * nx + x0 + lx];
+    }
+    cl.sync();
+    for (int s = 0; s < nsteps; ++s) {
+        split_stage_df<false>(cl, s0, nullptr, s1, a0, chunk, rank, x0, len, flag);
+        cl.sync();
+        split_stage_df<true>(cl, s1, s0, s0, a1, chunk, rank, x0, len, flag);
+        cl.sync();
+    }
+    for (int k = threadIdx.x; k < kNV * len; k += blockDim.x) {
+        const int i = k / len, lx = k - i * len;
+        f[(size_t)i * nx + x0 + lx] = s0[i * chunk + lx];
+    }
+}
+
 template <typename TS, bool kDF>
 void *small1d_func() { return (void *)small1d_kernel<TS, kDF>; }
 
-void *small1d_func_of(int prec)
+constexpr int kSplitDfMaxChunk = 128;     // two threads per cell within 256 threads
+
+void *small1d_func_of(int prec, int chunk)
 {
-    if (prec == CDBM_FP32_DF64) return small1d_func<float, true>();
+    if (prec == CDBM_FP32_DF64)
+        return chunk <= kSplitDfMaxChunk ? (void *)small1d_split_df_kernel : small1d_func<float, true>();
     if (prec == CDBM_FP32_BULK) return small1d_func<float, false>();
     return (void *)small1d_split_kernel;
 }
@@ -289,11 +395,12 @@ Small1D small1d_config(const StageArgs &a, int prec)
     const int chunk = (a.nx + cluster - 1) / cluster;
     cluster = (a.nx + chunk - 1) / chunk;            // no empty CTAs
     const size_t smem = 2 * kNV * (size_t)chunk * storage_bytes(prec);
-    // FP64: four threads per cell (split_stage), all cells of the CTA in one pass
-    const int per_cell = prec == CDBM_FP64 ? 4 : 1;
+    // FP64: four threads per cell (split_stage), df64: two (split_stage_df, up to
+    // kSplitDfMaxChunk cells), all cells of the CTA in one pass
+    const int per_cell = prec == CDBM_FP64 ? 4 : (prec == CDBM_FP32_DF64 && chunk <= kSplitDfMaxChunk ? 2 : 1);
     int threads = ((per_cell * chunk + 31) / 32) * 32;
     if (threads > 256) threads = 256;
-    void *func = small1d_func_of(prec);
+    void *func = small1d_func_of(prec, chunk);
     if (cluster > 8 && cudaFuncSetAttribute(func, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
         cudaGetLastError();
         return L;
