@@ -128,6 +128,7 @@ __global__ void __launch_bounds__(kStageThreads, stage_min_blocks(kDF))
 // per velocity and carries them to the next row in shared memory, so a y-term costs
 // 4 instead of 6 arithmetic instructions, with the same operations as stage_kernel.
 constexpr int kNY = 12;                             // velocities with a y-component
+constexpr size_t kMarchRowBytes = 2 * 12 * (kStageThreads + 2) * sizeof(double);   // FP64 x row buffers
 __host__ __device__ constexpr int yvel(int k)       // k-th velocity with diry != 0
 {
     return k < 2 ? 1 + 2 * k : (k < 6 ? k + 2 : (k < 8 ? 9 + 2 * (k - 6) : k + 4));
@@ -139,16 +140,17 @@ __global__ void __launch_bounds__(kStageThreads, stage_min_blocks(kDF))
 {
     // In double precision the x differences are shared as well: each thread computes
     // U_x = f_x - f_{x-s} of its cell once per velocity and reads U_{x+s}, U_{x-s} of
-    // its neighbours from a row buffer (two block barriers per row; the edge threads
-    // add the halo values), so an x-term costs 4 FP64 instructions plus a share of the
-    // halo instead of 6.  The operands and operations are those of nnd(), so the
+    // its neighbours from a row buffer (double-buffered in dynamic shared memory, so
+    // one block barrier per row; the edge threads add the halo values), so an x-term
+    // costs 4 FP64 instructions plus a share of the halo instead of 6.  The operands and operations are those of nnd(), so the
     // result is the same bit for bit.  In single precision the FP32 arithmetic is not
     // the scarce unit and the plain three-load form is kept.
     constexpr bool kShareX = !kSingle<TS>;
     constexpr int kNXV = 12;                          // velocities with an x component
     __shared__ TS carry_u[kNY][kStageThreads];
     __shared__ TS carry_n[kNY][kStageThreads];
-    __shared__ TS row_u[kShareX ? kNXV : 1][kShareX ? kStageThreads + 2 : 1];
+    extern __shared__ __align__(16) unsigned char march_dyn[];   // [2][kNXV][kStageThreads + 2] TS
+    TS(*const row_buf)[kStageThreads + 2] = reinterpret_cast<TS(*)[kStageThreads + 2]>(march_dyn);
     const int nx = a.nx, ny = a.ny;
     const int tid = threadIdx.x;
     const int x = blockIdx.x * blockDim.x + tid;
@@ -193,6 +195,9 @@ __global__ void __launch_bounds__(kStageThreads, stage_min_blocks(kDF))
     for (int y = y0; y < y1; ++y) {
         const size_t row = (size_t)y * nx;
         const size_t c = row + xc;
+        // row y writes buffer y & 1; its readers have passed the next row's barrier
+        // before row y + 2 writes the same buffer again
+        TS(*const row_u)[kStageThreads + 2] = row_buf + (kShareX ? (y & 1) * kNXV : 0);
         TS fs[kNV], o[kNV];
         if (active) {
 #pragma unroll
@@ -257,7 +262,6 @@ __global__ void __launch_bounds__(kStageThreads, stage_min_blocks(kDF))
                     ++k;
                 }
             }
-            __syncthreads();
         }
         if (active) {
             const size_t rp1 = (size_t)neighbour(y + 1, ny, a.bc_y) * nx + x;
@@ -740,6 +744,13 @@ StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count
         L.func = pair ? stage_march2_func(with_base, (a.nx & 1) == 0)
                  : prec == CDBM_FP32_BULK ? stage_func<float, false>(true, with_base, false)
                                           : stage_func<double, false>(true, with_base, false);
+        if (prec == CDBM_FP64) {
+            // the double-buffered x row buffer of stage_march_kernel<double>
+            L.smem = kMarchRowBytes;
+            if (cudaFuncSetAttribute(L.func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem) !=
+                cudaSuccess)
+                cudaGetLastError();   // the launch then reports the error
+        }
         if (pair) {
             // rows staged by cp.async: dynamic shared memory beside the static carries
             L.smem = kMarch2StageBytes;
