@@ -358,7 +358,8 @@ void build_stages(cdbm_ctx *c)
         a.bc_x = c->grid.bc_x;
         a.bc_y = c->grid.bc_y;
         fill_df_consts(a);
-        c->launch[s] = stage_launch_config(a, r.with_base, c->sm_count, c->precision, c->march_enabled);
+        c->launch[s] = stage_launch_config(a, r.with_base, c->sm_count, c->precision, c->march_enabled,
+                                           c->small_enabled);
     }
     c->small = small1d_config(c->stage[0], c->precision);
 }
@@ -620,7 +621,11 @@ cdbm_status cdbm_set_small_grid_path(cdbm_ctx *c, int enable)
 {
     if (!c) return CDBM_EINVAL;
     if (c->err) return c->err;
-    c->small_enabled = enable != 0;
+    if ((enable != 0) != c->small_enabled) {
+        c->small_enabled = enable != 0;
+        drop_graph(c);
+        build_stages(c);
+    }
     return CDBM_OK;
 }
 

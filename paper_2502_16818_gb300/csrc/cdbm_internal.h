@@ -168,9 +168,16 @@ struct StageLaunch {
     dim3 grid, block;
     size_t smem = 0;              // dynamic shared memory bytes
 };
-// allow_march = false keeps 2-D grids on the one-cell-per-thread stage kernel.
+// allow_march = false keeps 2-D grids on the one-cell-per-thread stage kernel;
+// allow_split = false keeps FP64 1-D grids on it too (no four-thread split).
 StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count, int prec,
-                                bool allow_march = true);
+                                bool allow_march = true, bool allow_split = true);
+
+// FP64 stage kernel for 1-D grids with each cell split over four threads
+// (cdbm_small1d.cu): kSplitFlatThreads threads per block, 4 nx threads in all.
+constexpr int kSplitFlatThreads = 128;
+constexpr int kSplitFlatMaxCells = 16384;
+void *split_flat_func(bool with_base);
 cudaError_t launch_stage(const StageLaunch &L, const void *g, const void *base, void *out,
                          const StageArgs &a, unsigned *flag, cudaStream_t s);
 

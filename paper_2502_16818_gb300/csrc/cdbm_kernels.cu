@@ -716,11 +716,19 @@ cudaError_t launch_field_means(const double *rho, const double *T, size_t n, dou
     return cudaGetLastError();
 }
 
-StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count, int prec, bool allow_march)
+StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count, int prec, bool allow_march,
+                                bool allow_split)
 {
     StageLaunch L;
     const bool flat = (a.ny == 1);
     const size_t cells = (size_t)a.nx * a.ny;
+    if (allow_split && flat && prec == CDBM_FP64 && a.nx <= kSplitFlatMaxCells) {
+        // short FP64 tubes: four threads per cell shorten the dependent chain of a stage
+        L.func = split_flat_func(with_base);
+        L.block = dim3(kSplitFlatThreads, 1, 1);
+        L.grid = dim3((unsigned)((4 * (size_t)a.nx + kSplitFlatThreads - 1) / kSplitFlatThreads), 1, 1);
+        return L;
+    }
     // The df64 state marches two columns per thread (stage_march2_kernel).
     const bool pair = prec == CDBM_FP32_DF64;
     const int cols = pair ? 2 * kStageThreads : kStageThreads;

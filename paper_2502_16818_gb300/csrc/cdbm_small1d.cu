@@ -123,53 +123,15 @@ __global__ void __launch_bounds__(256) small1d_kernel(TS *f, int nsteps, const S
     }
 }
 
-// FP64 variant with the work of a cell split over four threads, one per velocity
-// group: thread 4c + g of the CTA handles group g of cell c.  A stage of one cell
-// is a chain of dependent FP64 instructions whose latency, not throughput, bounds a
-// small grid (one warp per SM); splitting the cell shortens the chain about fourfold.
-// The four threads exchange their group components (s0, sx, sy) by warp shuffles and
-// each forms the moments, primitive variables and the shared part of the
-// equilibrium with the operations of conserved(), primitives() and equilibrium() in
-// the same order; each then builds and updates its own group's four velocities.
-// The compiler may fuse a multiply and an add differently than in the
-// one-thread-per-cell kernels, so the two agree to rounding, not bit for bit.
-__device__ __forceinline__ void split_stage(const cg::cluster_group &cl, const double *src, const double *base,
-                                            double *dst, const StageArgs &a, bool with_base, int chunk, int rank,
-                                            int x0, int len, unsigned *flag)
+// The arithmetic of one cell's group g in the four-thread split (the FP64 cluster
+// kernel and the flat split stage kernel): from the group's four values q, its base
+// values bs and x stencil values, the four updated values o.  The four threads of a
+// cell are lanes 4c .. 4c + 3 of one warp.
+__device__ __forceinline__ void split_cell(const StageArgs &a, int g, const double q[4], const double bs[4],
+                                           const double up2[4], const double up1[4], const double dn1[4],
+                                           bool with_base, bool live, unsigned *flag, double o[4])
 {
     const int t = threadIdx.x;
-    const int g = t & 3;                              // velocity group of this thread
-    const int lx0 = t >> 2;
-    const bool live = lx0 < len;
-    const int lx = live ? lx0 : len - 1;              // idle threads mirror the last cell
-    const int gx = x0 + lx;
-    const int nx = a.nx;
-    double q[4], bs[4], up2[4], up1[4], dn1[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        q[j] = src[(4 * g + j) * chunk + lx];
-        bs[j] = with_base ? base[(4 * g + j) * chunk + lx] : 0.0;
-    }
-    const bool inner = lx >= 2 && lx + 2 < len;
-    const int xm2 = neighbour(gx - 2, nx, a.bc_x), xm1 = neighbour(gx - 1, nx, a.bc_x);
-    const int xp1 = neighbour(gx + 1, nx, a.bc_x), xp2 = neighbour(gx + 2, nx, a.bc_x);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int i = 4 * g + j;
-        const int sx = dirx(i);
-        if (sx == 0) {
-            up2[j] = up1[j] = dn1[j] = 0.0;
-        } else if (inner) {
-            const double *p = src + i * chunk + lx;
-            up2[j] = p[sx > 0 ? -2 : 2];
-            up1[j] = p[sx > 0 ? -1 : 1];
-            dn1[j] = p[sx > 0 ? 1 : -1];
-        } else {
-            up2[j] = cluster_value(cl, src, chunk, rank, i, sx > 0 ? xm2 : xp2);
-            up1[j] = cluster_value(cl, src, chunk, rank, i, sx > 0 ? xm1 : xp1);
-            dn1[j] = cluster_value(cl, src, chunk, rank, i, sx > 0 ? xp1 : xm1);
-        }
-    }
     // group components, as conserved()
     double c0, cx, cy;
     if ((g & 1) == 0) {
@@ -217,7 +179,6 @@ __device__ __forceinline__ void split_stage(const cg::cluster_group &cl, const d
                                    : m6 * fma(B.B2[g], W4, B.B2[g - 1]);       // g = 1: b, g = 3: d
     double heq[4];
     equilibrium_group(B, g, e0, qv, s.q.jx, s.q.jy, s.T, u2, dlt, heq);
-    double o[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int i = 4 * g + j;
@@ -225,9 +186,103 @@ __device__ __forceinline__ void split_stage(const cg::cluster_group &cl, const d
         if (with_base) o[j] = fma(a.a_base, bs[j], o[j]);
         if (dirx(i) != 0) o[j] = fma(-a.lx[g], nnd(up2[j], up1[j], q[j], dn1[j]), o[j]);
     }
+}
+
+// FP64 variant with the work of a cell split over four threads, one per velocity
+// group: thread 4c + g of the CTA handles group g of cell c.  A stage of one cell
+// is a chain of dependent FP64 instructions whose latency, not throughput, bounds a
+// small grid (one warp per SM); splitting the cell shortens the chain about fourfold.
+// The four threads exchange their group components (s0, sx, sy) by warp shuffles and
+// each forms the moments, primitive variables and the shared part of the
+// equilibrium with the operations of conserved(), primitives() and equilibrium() in
+// the same order; each then builds and updates its own group's four velocities.
+// The compiler may fuse a multiply and an add differently than in the
+// one-thread-per-cell kernels, so the two agree to rounding, not bit for bit.
+__device__ __forceinline__ void split_stage(const cg::cluster_group &cl, const double *src, const double *base,
+                                            double *dst, const StageArgs &a, bool with_base, int chunk, int rank,
+                                            int x0, int len, unsigned *flag)
+{
+    const int t = threadIdx.x;
+    const int g = t & 3;                              // velocity group of this thread
+    const int lx0 = t >> 2;
+    const bool live = lx0 < len;
+    const int lx = live ? lx0 : len - 1;              // idle threads mirror the last cell
+    const int gx = x0 + lx;
+    const int nx = a.nx;
+    double q[4], bs[4], up2[4], up1[4], dn1[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        q[j] = src[(4 * g + j) * chunk + lx];
+        bs[j] = with_base ? base[(4 * g + j) * chunk + lx] : 0.0;
+    }
+    const bool inner = lx >= 2 && lx + 2 < len;
+    const int xm2 = neighbour(gx - 2, nx, a.bc_x), xm1 = neighbour(gx - 1, nx, a.bc_x);
+    const int xp1 = neighbour(gx + 1, nx, a.bc_x), xp2 = neighbour(gx + 2, nx, a.bc_x);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int i = 4 * g + j;
+        const int sx = dirx(i);
+        if (sx == 0) {
+            up2[j] = up1[j] = dn1[j] = 0.0;
+        } else if (inner) {
+            const double *p = src + i * chunk + lx;
+            up2[j] = p[sx > 0 ? -2 : 2];
+            up1[j] = p[sx > 0 ? -1 : 1];
+            dn1[j] = p[sx > 0 ? 1 : -1];
+        } else {
+            up2[j] = cluster_value(cl, src, chunk, rank, i, sx > 0 ? xm2 : xp2);
+            up1[j] = cluster_value(cl, src, chunk, rank, i, sx > 0 ? xm1 : xp1);
+            dn1[j] = cluster_value(cl, src, chunk, rank, i, sx > 0 ? xp1 : xm1);
+        }
+    }
+    double o[4];
+    split_cell(a, g, q, bs, up2, up1, dn1, with_base, live, flag, o);
     if (live) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) dst[(4 * g + j) * chunk + lx] = o[j];
+    }
+}
+
+// One FP64 stage of a 1-D grid as an ordinary launch with each cell split over four
+// threads (split_cell), for tubes too long for the cluster kernel.  With one thread
+// per cell a tube of a few thousand cells leaves about a warp per SM, and the chain
+// of dependent FP64 instructions of one cell, not the launch, sets the time of a
+// stage; four threads per cell shorten that chain.  Threads past the last cell
+// mirror it (they take part in the shuffles) and store nothing.
+template <bool kBase>
+__global__ void __launch_bounds__(kSplitFlatThreads) stage_split_flat_kernel(const double *__restrict__ g,
+                                                                             const double *base, double *out,
+                                                                             const StageArgs a, unsigned *flag)
+{
+    const int t = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    const int gq = t & 3;                             // velocity group of this thread
+    const int x0 = t >> 2;
+    const int nx = a.nx;
+    const bool live = x0 < nx;
+    const int x = live ? x0 : nx - 1;
+    const size_t P = (size_t)nx;                      // ny = 1
+    double q[4], bs[4], up2[4], up1[4], dn1[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        q[j] = g[(4 * gq + j) * P + x];
+        bs[j] = kBase ? base[(4 * gq + j) * P + x] : 0.0;
+    }
+    const int xm2 = neighbour(x - 2, nx, a.bc_x), xm1 = neighbour(x - 1, nx, a.bc_x);
+    const int xp1 = neighbour(x + 1, nx, a.bc_x), xp2 = neighbour(x + 2, nx, a.bc_x);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int i = 4 * gq + j;
+        const int sx = dirx(i);
+        const double *p = g + i * P;
+        up2[j] = sx == 0 ? 0.0 : p[sx > 0 ? xm2 : xp2];
+        up1[j] = sx == 0 ? 0.0 : p[sx > 0 ? xm1 : xp1];
+        dn1[j] = sx == 0 ? 0.0 : p[sx > 0 ? xp1 : xm1];
+    }
+    double o[4];
+    split_cell(a, gq, q, bs, up2, up1, dn1, kBase, live, flag, o);
+    if (live) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) out[(4 * gq + j) * P + x] = o[j];
     }
 }
 
@@ -376,6 +431,11 @@ void *small1d_func_of(int prec, int chunk)
 }
 
 }  // namespace
+
+void *split_flat_func(bool with_base)
+{
+    return with_base ? (void *)stage_split_flat_kernel<true> : (void *)stage_split_flat_kernel<false>;
+}
 
 Small1D small1d_config(const StageArgs &a, int prec)
 {
