@@ -146,7 +146,7 @@ cdbm_status cdbm_init(cdbm_ctx *ctx, const double *rho, const double *ux, const 
 cdbm_status cdbm_step(cdbm_ctx *ctx, int nsteps);
 
 /* Enables (default) or disables the small-grid paths of cdbm_step for 1-D grids: the
- * persistent cluster kernel, and for CDBM_FP64 tubes of up to 16384 cells the stage
+ * persistent cluster kernel, and for CDBM_FP64 tubes of up to 8192 cells the stage
  * kernel that splits each cell over four threads.  Disabled, those grids step with
  * the one-cell-per-thread stage kernel like any other. */
 cdbm_status cdbm_set_small_grid_path(cdbm_ctx *ctx, int enable);

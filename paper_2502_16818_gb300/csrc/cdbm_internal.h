@@ -176,7 +176,8 @@ StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count
 // FP64 stage kernel for 1-D grids with each cell split over four threads
 // (cdbm_small1d.cu): kSplitFlatThreads threads per block, 4 nx threads in all.
 constexpr int kSplitFlatThreads = 128;
-constexpr int kSplitFlatMaxCells = 16384;
+constexpr int kSplitFlatMaxCells = 8192;    // measured per stage: 8.8 against 10.0 us at 8192 cells,
+                                            // 16.3 against 10.7 us at 16384
 void *split_flat_func(bool with_base);
 cudaError_t launch_stage(const StageLaunch &L, const void *g, const void *base, void *out,
                          const StageArgs &a, unsigned *flag, cudaStream_t s);

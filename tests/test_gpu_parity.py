@@ -530,14 +530,14 @@ def test_misaligned_allocator_block_is_refused():
 @pytest.mark.parametrize("rk", [0, 1])
 @pytest.mark.parametrize("bc", [W.ZERO_GRADIENT, W.PERIODIC])
 def test_split_cell_stage_kernel_matches_one_thread_per_cell(rk, bc):
-    """FP64 tubes too long for the cluster kernel (up to 16384 cells) step with each
+    """FP64 tubes too long for the cluster kernel (up to 8192 cells) step with each
     cell split over four threads; switched off, with one thread per cell.  The split
     restates the same operations, the compiler may fuse a multiply and an add
     differently, so the two agree to rounding: 1e-12 of max |f| after 42 steps, for
     a cell count that is not a multiple of the block's 32 cells and for the largest
     tube."""
     from paper_2502_16818_gb300 import Solver, cdbm
-    for nx in (1025, 3001, 16384):
+    for nx in (1025, 3001, 8192):
         w = W.random_blocks(nx, 1, seed=nx, bc=(bc, W.PERIODIC))
         w.dx = 1.0 / nx
         w.dt = 0.2 * w.dx / 2.2
