@@ -468,7 +468,7 @@ def test_small_grid_cluster_path_matches_stage_launches(prec, rk, bc):
 
 
 @pytest.mark.parametrize("prec", [0, 1, 2])
-@pytest.mark.parametrize("shape", [(1026, 600), (1027, 600), (514, 2100)])
+@pytest.mark.parametrize("shape", [(1026, 600), (1027, 600), (514, 2100), (3, 4096), (2, 4096)])
 @pytest.mark.parametrize("bc", [(W.PERIODIC, W.PERIODIC), (W.ZERO_GRADIENT, W.ZERO_GRADIENT)])
 def test_row_marching_matches_one_cell_per_thread(prec, shape, bc):
     """The row-marching stage kernels (y differences carried up runs of rows; FP64
@@ -477,7 +477,8 @@ def test_row_marching_matches_one_cell_per_thread(prec, shape, bc):
     stage kernel apply the same operations to every cell, so 7 steps agree bit for
     bit.  The shapes select runs of 8, 4 and 2 rows, even and odd nx (the aligned
     float2 and the per-column forms of the two-column kernel, and a last thread with
-    one column), and partial blocks and runs."""
+    one column), partial blocks and runs, and grids two or three cells wide whose x
+    stencil wraps onto itself."""
     from paper_2502_16818_gb300 import Solver, cdbm
     nx, ny = shape
     w = W.random_blocks(nx, ny, seed=nx + ny, bc=bc)
