@@ -118,6 +118,90 @@ __device__ __forceinline__ void tube_stage(const TS *g, const TS *base, TS *out,
     }
 }
 
+// The FP64 stage of one tube with the x differences shared: the block covers a chunk
+// of blockDim cells at a time; each thread computes U = f_x - f_{x-s} of its cell once
+// per velocity into a row buffer in shared memory, the chunk's edge threads add the
+// values beyond it (the tube's zero-gradient ends included, through the clamped
+// indices), and each cell reads U of its neighbours there: 4 instead of 6 FP64
+// instructions per x term, with the operands and operations of nnd(), so the result
+// is the same bit for bit.  All threads run the same chunk loop and reach the block
+// barriers.
+template <int kStage, int kThreads>
+__device__ __forceinline__ void tube_stage_shared_x(const double *g, const double *base, double *out, long long P,
+                                                    const TubeInfo &t, const ClassConsts &C, double a_self,
+                                                    double a_base, unsigned *flag, double (*row_u)[kThreads + 2])
+{
+    constexpr bool kBase = kStage == 1;
+    const int nx = t.nx;
+    const double *lx = t.lx[kStage];
+    const int tid = threadIdx.x;
+    for (int xb = 0; xb < nx; xb += kThreads) {
+        const int x = xb + tid;
+        const bool active = x < nx;
+        const int xc = active ? x : nx - 1;
+        const int last = (nx - xb < kThreads ? nx - xb : kThreads) - 1;      // last active thread
+        const int xm2 = xc >= 2 ? xc - 2 : 0, xm1 = xc >= 1 ? xc - 1 : 0;
+        const int xp1 = xc + 1 < nx ? xc + 1 : nx - 1, xp2 = xc + 2 < nx ? xc + 2 : nx - 1;
+        double fs[kNV], o[kNV];
+        if (active) {
+#pragma unroll
+            for (int i = 0; i < kNV; ++i) fs[i] = g[i * P + x];
+            const Prim s = primitives<false>(fs, C.m, 0.0, 0.0, flag);
+            double heq[kNV];
+            equilibrium<false>(C.eq[kStage], C.m, s.q.rho, s.q.E, s.q.jx, s.q.jy, s.ux, s.uy, s.ru2, s.jyuy, s.p,
+                               s.T, heq);
+            int k = 0;
+#pragma unroll
+            for (int i = 0; i < kNV; ++i) {
+                o[i] = fma(a_self, fs[i], heq[i]);
+                if (kBase) o[i] = fma(a_base, base[i * P + x], o[i]);
+                if (dirx(i) != 0) {
+                    row_u[k][tid + 1] = fs[i] - g[i * P + (dirx(i) > 0 ? xm1 : xp1)];   // a of nnd()
+                    ++k;
+                }
+            }
+            if (tid == 0) {                           // U left of the chunk
+                int k2 = 0;
+#pragma unroll
+                for (int i = 0; i < kNV; ++i) {
+                    if (dirx(i) == 0) continue;
+                    const double *gp = g + i * P;
+                    row_u[k2][0] = dirx(i) > 0 ? gp[xm1] - gp[xm2] : gp[xm1] - fs[i];
+                    ++k2;
+                }
+            }
+            if (tid == last) {                        // U right of the chunk
+                int k2 = 0;
+#pragma unroll
+                for (int i = 0; i < kNV; ++i) {
+                    if (dirx(i) == 0) continue;
+                    const double *gp = g + i * P;
+                    row_u[k2][last + 2] = dirx(i) > 0 ? gp[xp1] - fs[i] : gp[xp1] - gp[xp2];
+                    ++k2;
+                }
+            }
+        }
+        __syncthreads();
+        if (active) {
+            int k = 0;
+#pragma unroll
+            for (int i = 0; i < kNV; ++i) {
+                if (dirx(i) != 0) {
+                    const int s = dirx(i);
+                    const double av = row_u[k][tid + 1];          // c - u1
+                    const double bv = row_u[k][tid + 1 + s];      // d1 - c
+                    const double ev = row_u[k][tid + 1 - s];      // u1 - u2
+                    const double tt = minmod(bv, av) - minmod(av, ev);
+                    o[i] = fma(-lx[i >> 2], fma(0.5, tt, av), o[i]);
+                    ++k;
+                }
+                out[i * P + x] = o[i];
+            }
+        }
+        __syncthreads();                              // the next chunk rewrites the buffer
+    }
+}
+
 // The df64 stage of one tube with two cells per thread: each thread takes the
 // pairs (x, x + 1) of the tube (x even; x + 1 = x for an odd last cell, computed
 // twice and stored once) and applies every operation of tube_stage<float, kStage,
@@ -180,13 +264,19 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks(kThreads, kDF)) bat
 {
     const TS as0 = pick<TS>(a.a_self[0], a.a_self_f[0]), as1 = pick<TS>(a.a_self[1], a.a_self_f[1]);
     const TS ab0 = pick<TS>(a.a_base[0], a.a_base_f[0]), ab1 = pick<TS>(a.a_base[1], a.a_base_f[1]);
+    // x row buffer of the FP64 stage (a placeholder for the single-precision states)
+    __shared__ double row_u[kSingle<TS> ? 1 : 12][kSingle<TS> ? 1 : kThreads + 2];
     for (int w = work_off[blockIdx.x]; w < work_off[blockIdx.x + 1]; ++w) {
         const TubeInfo &t = tubes[work[w]];
         const ClassConsts &C = a.cls[t.cls];
         TS *ft = f + t.offset;
         TS *f1t = f1 + t.offset;
         for (int s = 0; s < nsteps; ++s) {
-            if constexpr (kDF) {
+            if constexpr (!kSingle<TS>) {
+                tube_stage_shared_x<0, kThreads>(ft, nullptr, f1t, a.P, t, C, as0, ab0, flag, row_u);
+                __syncthreads();
+                tube_stage_shared_x<1, kThreads>(f1t, ft, ft, a.P, t, C, as1, ab1, flag, row_u);
+            } else if constexpr (kDF) {
                 tube_stage2<0>(ft, nullptr, f1t, a.P, t, C, a.a_self_f2[0], a.a_base_f2[0], flag);
                 __syncthreads();
                 tube_stage2<1>(f1t, ft, ft, a.P, t, C, a.a_self_f2[1], a.a_base_f2[1], flag);
