@@ -50,8 +50,8 @@ FP64_LANES_PER_CLK_PER_SM = 2       # 1.25 TFLOP/s nominal FP64 / (2 flops x 152
 # the stage kernels; valid only while the code of the kernel sources (comments
 # stripped) hashes to TRAFFIC_SHA.
 # Captured at 1024^2 (134 MB per plane set, above L2) and scaled by 16 cells-fold.
-TRAFFIC_SHA = "8c6388fb4409f177"
-TRAFFIC_BYTES_PER_LAUNCH = 5.110e9
+TRAFFIC_SHA = "4b0dfe90da4c110d"
+TRAFFIC_BYTES_PER_LAUNCH = 5.103e9
 
 
 STAGE_SOURCES = ("cdbm_device.cuh", "cdbm_kernels.cu", "cdbm_internal.h")

@@ -198,8 +198,10 @@ __device__ __forceinline__ void equilibrium(const EqBlocks &B, const ModelConsts
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
         const double *S = B.S + 4 * g;
-        s0[g] = fma(S[3], m1416, fma(S[2], ru2, fma(S[1], E, S[0] * rho)));
-        if (kShift) s0[g] -= s0_shift[g];
+        if (kShift)   // the reference group value enters the innermost product as its addend
+            s0[g] = fma(S[3], m1416, fma(S[2], ru2, fma(S[1], E, fma(S[0], rho, -s0_shift[g]))));
+        else
+            s0[g] = fma(S[3], m1416, fma(S[2], ru2, fma(S[1], E, S[0] * rho)));
     }
     const double dqa = d57 * fma(B.B1[1], W4, B.B1[0]);
     const double dqc = d57 * fma(B.B1[3], W4, B.B1[2]);
