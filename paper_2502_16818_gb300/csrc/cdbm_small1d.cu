@@ -10,7 +10,9 @@
 // are separated by the cluster barrier, a hardware barrier over the co-scheduled
 // CTAs (no software spin-wait).  In single precision the per-cell arithmetic is
 // that of the flat stage kernel in the same order, so the result is the same bit for
-// bit; the FP64 variant splits a cell over four threads (split_stage).
+// bit; the df64 variant splits a cell over two threads (split_stage_df) and the FP64
+// variant over four (split_stage).  The FP64 four-thread split also runs as an
+// ordinary stage launch for tubes too long for one cluster (stage_split_flat_kernel).
 #include <cooperative_groups.h>
 
 #include "cdbm_stage.cuh"
