@@ -325,25 +325,54 @@ void cdbm_batch_destroy(cdbm_batch *b);
  *   grid, vset, I, tau, dt : as for cdbm_create, with the same validation.
  *   f            : device pointer to the caller's state [16][ny][nx] (for example from
  *                  cdbm_get_state or an equilibrium the caller built), advanced in
- *                  place by nsteps >= 0 two-stage TVD Runge-Kutta steps; the result
- *                  equals cdbm_step's on the same state.
+ *                  place by nsteps >= 0 two-stage TVD Runge-Kutta steps.  The result
+ *                  matches cdbm_step's on the same state to rounding (within 1e-12
+ *                  relative max-norm): both apply the same per-cell operations, but
+ *                  on a short 1-D grid cdbm_step may run them in its cluster kernel,
+ *                  whose compiled arithmetic can round differently.  On 2-D grids
+ *                  both run the same stage kernels and agree bit for bit.
  *   cuda_stream  : stream for the work (NULL = legacy stream).
  * Scratch: the stage-1 buffer and the error flag live in one fixed device array of
  * the library (16 * CDBM_NOALLOC_MAX_CELLS doubles plus 256 bytes, i.e. 4 MiB), which
  * every GPU that loads the library holds until the process exits.  The call makes no
  * cudaMalloc/cudaFree or other allocating call.  The first call on a device looks up
- * that array's device address (cudaGetSymbolAddress, with the device current); make
- * that first call before any stream capture.  All calls on a device share the array
- * and it keeps the last call's contents (the flag is cleared at the start of each
- * call), so calls that overlap on the GPU -- on different streams or host threads --
- * race and must be serialised by the caller.
- * Synchronous: returns after the work has finished.  Errors: CDBM_EINVAL (as
+ * that array's device address (cudaGetSymbolAddress, with the device current).  All
+ * calls on a device share the array and it keeps the last call's contents (the flag
+ * is cleared at the start of each call), so calls that overlap on the GPU -- on
+ * different streams or host threads -- race and must be serialised by the caller.
+ * Synchronous: every call ends by copying the flag to the host and waiting for its
+ * stream, so it cannot be called while a stream is being captured into a CUDA graph.
+ * Errors: CDBM_EINVAL (as
  * cdbm_create, f NULL, nsteps < 0, or nx * ny > CDBM_NOALLOC_MAX_CELLS),
  * CDBM_ESINGULAR, CDBM_ECUDA, CDBM_ENONPHYS (the state went non-physical; f holds the
  * result of the last step).  Messages go to cdbm_last_error(NULL).
  */
 cdbm_status cdbm_step_noalloc(const cdbm_grid *grid, const cdbm_vset *vset, double I, double tau,
                               double dt, double *f, int nsteps, void *cuda_stream);
+
+/* ------------------------------------------------------------------------------
+ * Diagnostics.  The paper has no counterpart: each runs one device building block,
+ * or one hardware rate probe, on its own, so that tests can bound a building block
+ * against IEEE arithmetic and the benchmark can measure the rate that bounds the
+ * FP64 stage kernels in the same process.  Both are asynchronous on cuda_stream
+ * (NULL = legacy stream); messages go to cdbm_last_error(NULL).
+ * ---------------------------------------------------------------------------- */
+
+/* y[k] = 1 / x[k] for 0 <= k < n, by the reciprocal the kernels use for 1 / rho
+ * (the hardware estimate refined by one cubic Newton-Raphson step).  x, y: device
+ * arrays of n doubles; x positive, finite and normal (subnormal inputs are flushed
+ * to zero by the estimate).  Errors: CDBM_EINVAL (n < 0, NULL pointer with n > 0),
+ * CDBM_ECUDA. */
+cdbm_status cdbm_diag_rcp64(const double *x, double *y, long long n, void *cuda_stream);
+
+/* FP64 fused multiply-add probe: blocks x threads threads each run 8 independent
+ * chains of `iters` dependent FMAs and write one double to out (device,
+ * blocks * threads doubles, caller-owned).  *flops (host, may be NULL) receives the
+ * flop count, 2 per FMA; the caller times the launch with events on cuda_stream.
+ * Errors: CDBM_EINVAL (NULL out, blocks < 1, threads not a multiple of 32 in
+ * [32, 1024], iters < 1), CDBM_ECUDA. */
+cdbm_status cdbm_diag_fp64_fma(double *out, int blocks, int threads, int iters, void *cuda_stream,
+                               double *flops);
 
 #ifdef __cplusplus
 }

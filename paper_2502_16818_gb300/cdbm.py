@@ -31,7 +31,8 @@ EXPORTS = ("cdbm_create", "cdbm_set_rk", "cdbm_init", "cdbm_step", "cdbm_set_sma
            "cdbm_batch_create", "cdbm_batch_init", "cdbm_batch_step", "cdbm_batch_autotune",
            "cdbm_batch_set_tile", "cdbm_batch_macros", "cdbm_batch_info", "cdbm_batch_sync",
            "cdbm_batch_last_error", "cdbm_batch_destroy", "cdbm_adjoint_forward",
-           "cdbm_adjoint_backward", "cdbm_adjoint_set_limiter", "cdbm_macros_vjp")
+           "cdbm_adjoint_backward", "cdbm_adjoint_set_limiter", "cdbm_macros_vjp",
+           "cdbm_diag_rcp64", "cdbm_diag_fp64_fma")
 CDBM_NOALLOC_MAX_CELLS = 32768
 
 
@@ -116,6 +117,8 @@ def load(path: str | None = None):
         "cdbm_adjoint_backward": ([ctx, _vp, _vp, _vp, _vp, _vp, _dp], ctypes.c_int),
         "cdbm_adjoint_set_limiter": ([ctx, ctypes.c_int], ctypes.c_int),
         "cdbm_macros_vjp": ([ctx, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+        "cdbm_diag_rcp64": ([_vp, _vp, ctypes.c_longlong, _vp], ctypes.c_int),
+        "cdbm_diag_fp64_fma": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _dp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -256,6 +259,23 @@ def cdbm_macros_vjp(ctx, rho_bar, ux_bar, uy_bar, T_bar, fbar):
     lib = load()
     _check(lib, ctx, lib.cdbm_macros_vjp(ctx, rho_bar or None, ux_bar or None, uy_bar or None, T_bar or None,
                                          fbar))
+
+
+def cdbm_diag_rcp64(x, y, n, stream=0):
+    """y = 1 / x (device addresses, n doubles) by the kernels' reciprocal."""
+    lib = load()
+    _check(lib, None, lib.cdbm_diag_rcp64(ctypes.c_void_p(x), ctypes.c_void_p(y), int(n),
+                                          ctypes.c_void_p(stream)))
+
+
+def cdbm_diag_fp64_fma(out, blocks, threads, iters, stream=0) -> float:
+    """Launches the FP64 FMA probe (out: device address of blocks * threads doubles);
+    returns its flop count."""
+    lib = load()
+    fl = ctypes.c_double()
+    _check(lib, None, lib.cdbm_diag_fp64_fma(ctypes.c_void_p(out), int(blocks), int(threads), int(iters),
+                                             ctypes.c_void_p(stream), ctypes.byref(fl)))
+    return fl.value
 
 
 def _bcheck(lib, b, status):

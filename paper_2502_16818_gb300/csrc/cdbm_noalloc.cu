@@ -124,7 +124,7 @@ extern "C" cdbm_status cdbm_step_noalloc(const cdbm_grid *grid, const cdbm_vset 
     // f1 = f + dt L(f); f <- f/2 + (f1 + dt L(f1))/2.
     const double h = dt / tau;
     const double alpha[2] = {0.0, 0.5}, beta[2] = {1.0, 0.5}, gamma[2] = {1.0, 0.5};
-    StageArgs a[2];
+    StageArgs a[2]{};   // fields the FP64 stage kernels do not read stay zero
     StageLaunch L[2];
     for (int s = 0; s < 2; ++s) {
         a[s].eq = scaled(eq, gamma[s] * h);
