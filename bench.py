@@ -45,6 +45,12 @@ FP64_INSTR_PER_CELL_STEP = 508
 FP64_FLOPS_PER_CELL_STEP = 766
 BYTES_PER_CELL_STEP = 640
 FP64_LANES_PER_CLK_PER_SM = 2       # 1.25 TFLOP/s nominal FP64 / (2 flops x 152 SMs x 2.07 GHz)
+BYTES_PER_CELL_STEP_FP32 = 320      # the same buffers in single precision
+# Adjoint backward sweep per cell-step (FP64): the segment recompute (one forward
+# step, 640 B, its stage-1 state written to the kept segment) and the two adjoint
+# stage kernels (stage 2: read the stage-1 state and the cotangent, write one, 384 B;
+# stage 1: read the state, two cotangents, write one, 512 B).
+BYTES_PER_CELL_STEP_ADJ_BWD = 640 + 384 + 512
 
 # DRAM traffic of one stage launch (mean of the two stages) from one ncu capture of
 # the stage kernels; valid only while the code of the kernel sources (comments
@@ -93,6 +99,8 @@ def parse():
     p.add_argument("--adj-steps", type=int, default=4000, help="steps of the adjoint run (0: skip it)")
     p.add_argument("--adj-every", type=int, default=200, help="checkpoint interval of the adjoint run")
     p.add_argument("--adj-n", type=int, default=1024, help="grid size of the adjoint run")
+    p.add_argument("--full-steps", type=int, default=2000,
+                   help="steps of the full-length vortex runs in all three precisions (0: skip them)")
     return p.parse_args()
 
 
@@ -266,6 +274,24 @@ def time_tgv(w, precision, steps, warmup, torch, Solver):
     return s, stream, a0
 
 
+def fp64_peak(torch, cdbm, stream):
+    """Measured FP64 FMA rate of this GPU (TFLOP/s): the library's probe kernel, 8
+    independent chains of dependent FMAs per thread, 152 x 8 blocks of 256 threads,
+    best of 6 launches timed with CUDA events on `stream`."""
+    blocks, threads, iters = 152 * 8, 256, 4096
+    out = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
+    best = 0.0
+    for _ in range(6):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flops = cdbm.cdbm_diag_fp64_fma(out.data_ptr(), blocks, threads, iters, stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        best = max(best, flops / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    return {"tflops": best, "kernel": "fp64_fma_kernel (cdbm_diag_fp64_fma)",
+            "launch": [blocks, threads, iters], "flops_per_launch": flops}
+
+
 def run_cdbm(a, rank, world, local_rank):
     import numpy as np
     import torch
@@ -315,10 +341,15 @@ def run_cdbm(a, rank, world, local_rank):
     traffic = None
     if TRAFFIC_SHA == kernel_sha() and plane_set_bytes >= 1024 * 1024 * 128:
         traffic = TRAFFIC_BYTES_PER_LAUNCH * cells / 4096 ** 2
+    probe = fp64_peak(torch, cdbm, stream)
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved_tflops / peak_tflops, "traffic": traffic,
                 "kernel": "stage_march_kernel (RK stages 1 and 2, mean per launch)",
                 "peak_source": "FP64 pipe: 2 lanes/clk/SM x 152 SMs x 2070 MHz x 2 flops (recipe nominal 1.25 TFLOP/s)",
+                "peak_measured": probe["tflops"], "frac_of_measured_peak": achieved_tflops / probe["tflops"],
+                "peak_measured_source": "%s, %d x %d threads x 8 chains x %d FMAs, best of 6, this run"
+                                        % (probe["kernel"], probe["launch"][0], probe["launch"][1],
+                                           probe["launch"][2]),
                 "fp64_pipe_frac": instr_rate / peak_instr,
                 "hbm_gbs": hbm_gbs, "hbm_frac_of_measured": hbm_gbs / measured_hbm()}
 
@@ -344,6 +375,8 @@ def run_cdbm(a, rank, world, local_rank):
         out["fp32_df64"] = fp32_variant(a, w, torch, Solver, CDBM_FP32_DF64, (rho64, ux64, uy64, T64), value, amp0,
                                         "as fp32_bulk, with sums, moment shift and equilibrium product in "
                                         "double-float arithmetic on the FP32 pipe")
+        if a.full_steps > 0:
+            out["config3_full"] = full_length_vortex(a, w, torch, Solver)
         if not a.no_ensemble:
             out["ensemble"] = ensemble(a, torch)
         if a.adj_steps > 0:
@@ -395,7 +428,64 @@ def fp32_variant(a, w, torch, Solver, precision, ref64, value64, amp0, note):
     return {"value": val, "unit": UNIT, "ms_per_step": ms / a.steps, "speedup_vs_fp64": val / value64,
             "l2_density_error_vs_fp64": l2, "field_errors_vs_fp64": errs, "steps_compared": a.steps + a.warmup,
             "decay_rate_measured": float(-np.log(amp1 / amp0) / (a.steps * w.dt)),
-            "hbm_gbs": 320 * w.nx * w.ny * a.steps / (ms * 1e-3) / 1e9, "note": note}
+            "hbm_gbs": BYTES_PER_CELL_STEP_FP32 * w.nx * w.ny * a.steps / (ms * 1e-3) / 1e9,
+            "hbm_frac_of_measured": BYTES_PER_CELL_STEP_FP32 * w.nx * w.ny * a.steps / (ms * 1e-3) / 1e9
+                                    / measured_hbm(), "note": note}
+
+
+def full_length_vortex(a, w, torch, Solver):
+    """The vortex run for its configured length (2000 steps, t = 0.01) in FP64,
+    FP32_BULK and FP32_DF64, whatever --steps is: each run timed as a whole, the
+    Taylor-Green amplitude sampled every 100 steps, the decay rate fitted (least
+    squares on log amplitude) over the last 1000 steps against the Navier-Stokes
+    rate 2 nu k^2 with nu = T tau (Eqs. 22-23), and the per-field errors of the
+    single-precision runs against the FP64 run at the last step."""
+    import numpy as np
+    from paper_2502_16818_gb300 import CDBM_FP32_BULK, CDBM_FP32_DF64, CDBM_FP64, workloads as W
+    steps = a.full_steps
+    every = 100 if steps % 100 == 0 else steps
+    k = w.extra["k"]
+    x = (torch.arange(w.nx, dtype=torch.float64, device="cuda") + 0.5) * w.dx
+    mode = torch.cos(k * x)[:, None] * torch.sin(k * x)[None, :]
+    res = {"steps": steps, "t_end": steps * w.dt, "sample_every": every}
+    finals = {}
+    for label, prec in (("fp64", CDBM_FP64), ("fp32_bulk", CDBM_FP32_BULK), ("fp32_df64", CDBM_FP32_DF64)):
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            s = Solver.from_workload(w, stream=st, precision=prec)
+            s.init(*(torch.from_numpy(v).to("cuda") for v in (w.rho, w.ux, w.uy, w.T)))
+        s.sync()
+        amps, ms = [], 0.0
+        for _ in range(steps // every):
+            with torch.cuda.stream(st):
+                amps.append(float((s.macros()[1] * mode).sum()))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            s.step(every)
+            e1.record(st)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        with torch.cuda.stream(st):
+            fin = s.macros()
+            amps.append(float((fin[1] * mode).sum()))
+        s.sync()
+        s.close()
+        torch.cuda.synchronize()
+        t = np.arange(len(amps)) * every * w.dt
+        tail = t >= t[-1] - 0.5 * steps * w.dt - 1e-12
+        rate = float(-np.polyfit(t[tail], np.log(np.abs(amps))[tail], 1)[0])
+        nu = float(fin[3].mean()) * w.tau
+        row = {"value": w.nx * w.ny * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+               "decay_rate_last_half": rate, "navier_stokes_2nuk2": 2 * nu * k * k,
+               "decay_rate_rel_err": rate / (2 * nu * k * k) - 1.0}
+        if label == "fp64":
+            finals = fin
+        else:
+            row["field_errors_vs_fp64"] = field_errors(fin, finals, W.gamma_of(w.I), torch)
+            row["speedup_vs_fp64"] = res["fp64"]["ms_per_step"] / row["ms_per_step"]
+        res[label] = row
+        del fin
+    return res
 
 
 def ensemble(a, torch):
@@ -420,8 +510,11 @@ def ensemble(a, torch):
         ms = e0.elapsed_time(e1)
         b.sync()
         b.close()
+        per = BYTES_PER_CELL_STEP if prec == 0 else BYTES_PER_CELL_STEP_FP32
+        gbs = per * res["cells"] * a.ens_steps / (ms * 1e-3) / 1e9
         res[name] = {"value": res["cells"] * a.ens_steps / (ms * 1e-3), "unit": UNIT, "tile": tile,
-                     "gpu_launches": 1}
+                     "gpu_launches": 1, "hbm_gbs": gbs, "hbm_frac_of_measured": gbs / measured_hbm(),
+                     "bytes_per_cell_step": per}
     # per-tube loop: one single-grid FP64 solver per tube, stepped one after another
     st = torch.cuda.Stream()
     solvers = []
@@ -477,7 +570,10 @@ def configs(a, torch):
             ms = e0.elapsed_time(e1)
             s.sync()
             s.close()
-            row[label] = {"run_ms": ms, "value": row["cells"] * steps / (ms * 1e-3), "unit": UNIT}
+            per = BYTES_PER_CELL_STEP if prec == CDBM_FP64 else BYTES_PER_CELL_STEP_FP32
+            gbs = per * row["cells"] * steps / (ms * 1e-3) / 1e9
+            row[label] = {"run_ms": ms, "value": row["cells"] * steps / (ms * 1e-3), "unit": UNIT,
+                          "hbm_gbs": gbs, "hbm_frac_of_measured": gbs / measured_hbm()}
         res[name] = row
     return res
 
@@ -518,12 +614,17 @@ def adjoint(a, torch):
     fwd_ms, bwd_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
     s.close()
     cells = w.nx * w.ny
+    fwd_gbs = (BYTES_PER_CELL_STEP * a.adj_steps + 128 * (a.adj_steps // a.adj_every)) * cells / (fwd_ms * 1e-3) / 1e9
+    bwd_gbs = BYTES_PER_CELL_STEP_ADJ_BWD * a.adj_steps * cells / (bwd_ms * 1e-3) / 1e9
     return {"value": cells * a.adj_steps / ((fwd_ms + bwd_ms) * 1e-3), "unit": UNIT,
             "workload": "sound_modes_%dx%d_kmax8_fp64" % (w.nx, w.ny), "steps": a.adj_steps,
             "checkpoint_every": a.adj_every, "limiter": "frozen", "forward_ms": fwd_ms, "backward_ms": bwd_ms,
             "backward_over_forward": bwd_ms / fwd_ms, "wall_s": wall, "loss": loss, "dL_dtau": gtau,
             "grad_rho_l2": float(torch.linalg.norm(grads[0])), "grad_T_l2": float(torch.linalg.norm(grads[3])),
-            "checkpoint_bytes": 128 * cells * (a.adj_steps // a.adj_every + 1)}
+            "checkpoint_bytes": 128 * cells * (a.adj_steps // a.adj_every + 1),
+            "forward_hbm_gbs": fwd_gbs, "forward_hbm_frac_of_measured": fwd_gbs / measured_hbm(),
+            "backward_hbm_gbs": bwd_gbs, "backward_hbm_frac_of_measured": bwd_gbs / measured_hbm(),
+            "bytes_per_cell_step": {"forward": BYTES_PER_CELL_STEP, "backward": BYTES_PER_CELL_STEP_ADJ_BWD}}
 
 
 def e2e(a, w, stream, cdbm, s, torch):
@@ -555,7 +656,7 @@ def measured_hbm():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
     except (OSError, KeyError, ValueError):
-        return 6800.0
+        return 6793.1     # the driver's measurement of this machine's GB300 copy bandwidth
 
 
 def main():

@@ -82,10 +82,31 @@ def test_fp32_sod_full_length(prec):
 
 
 def test_fp32_lax_2000_steps(prec):
-    """Lax tube, 2000 steps (the ensemble tubes run 1000).  Over the full 10000 steps
-    the single-precision state ends at 3.5e-5 relative L2 density error, carried by
-    the shock and contact, which sits above the 1e-5 bar."""
+    """Lax tube, 2000 steps (the ensemble tubes run 1000), under the 1e-5 bar."""
     check(W.lax(nx=2000, I=0.0), 2000, "lax", prec)
+
+
+# Lax at its configured 10^4 steps: measured on a GB300 against the oracle
+#                   rho L2    rho max   T L2      T max     u max / scale
+#   FP32_BULK       3.50e-5   3.46e-4   4.03e-5   1.30e-4   2.77e-4
+#   FP32_DF64       3.07e-5   1.75e-4   3.77e-5   8.08e-5   1.39e-4
+# The density error grows linearly with the steps (3.6e-6, 1.1e-5, 1.9e-5, 2.7e-5,
+# 3.5e-5 at 2000 .. 10000 steps): the moving shock and contact turn the float
+# rounding of every stage update (2^-24 of a deviation that is as large as F in this
+# tube, T spans 1.1 .. 7.9) into a slowly growing position error.  The FP64 state
+# stays within 8e-13 of the oracle.  This configuration is held to its measured bar.
+LAX_FULL_L2_RHO = 5e-5
+LAX_FULL_MAX_UT = 5e-4
+
+
+def test_fp32_lax_full_length(prec):
+    w = W.lax(nx=2000, I=0.0)
+    got = run_fp32(w, 10000, prec)
+    m = model_of(w)
+    ref = oracle.macros(m, oracle.step(m, oracle.init(m, w.rho, w.ux, w.uy, w.T), 10000))
+    e = errors(got, ref, W.gamma_of(w.I))
+    assert e["rho_l2"] <= LAX_FULL_L2_RHO, e
+    assert e["u_max"] <= LAX_FULL_MAX_UT and e["T_max"] <= LAX_FULL_MAX_UT, e
 
 
 @pytest.mark.parametrize("I", [0.0, 3.0])
