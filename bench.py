@@ -274,22 +274,27 @@ def time_tgv(w, precision, steps, warmup, torch, Solver):
     return s, stream, a0
 
 
-def fp64_peak(torch, cdbm, stream):
+def fp64_peak(torch, cdbm, stream, local_rank=0, launches=40):
     """Measured FP64 FMA rate of this GPU (TFLOP/s): the library's probe kernel, 8
     independent chains of dependent FMAs per thread, 152 x 8 blocks of 256 threads,
-    best of 6 launches timed with CUDA events on `stream`."""
+    each launch timed with CUDA events on `stream` (about 16 ms each; best and
+    median of `launches`), SM clocks sampled meanwhile."""
     blocks, threads, iters = 152 * 8, 256, 4096
     out = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
-    best = 0.0
-    for _ in range(6):
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    rates = []
+    for _ in range(launches):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         flops = cdbm.cdbm_diag_fp64_fma(out.data_ptr(), blocks, threads, iters, stream.cuda_stream)
         e1.record(stream)
         e1.synchronize()
-        best = max(best, flops / (e0.elapsed_time(e1) * 1e-3) / 1e12)
-    return {"tflops": best, "kernel": "fp64_fma_kernel (cdbm_diag_fp64_fma)",
-            "launch": [blocks, threads, iters], "flops_per_launch": flops}
+        rates.append(flops / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    clocks = sampler.stop()
+    return {"tflops": max(rates), "tflops_median": statistics.median(rates),
+            "kernel": "fp64_fma_kernel (cdbm_diag_fp64_fma)", "launch": [blocks, threads, iters],
+            "flops_per_launch": flops, "launches": launches, "clocks": clocks}
 
 
 def run_cdbm(a, rank, world, local_rank):
@@ -341,15 +346,16 @@ def run_cdbm(a, rank, world, local_rank):
     traffic = None
     if TRAFFIC_SHA == kernel_sha() and plane_set_bytes >= 1024 * 1024 * 128:
         traffic = TRAFFIC_BYTES_PER_LAUNCH * cells / 4096 ** 2
-    probe = fp64_peak(torch, cdbm, stream)
+    probe = fp64_peak(torch, cdbm, stream, local_rank)
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved_tflops / peak_tflops, "traffic": traffic,
                 "kernel": "stage_march_kernel (RK stages 1 and 2, mean per launch)",
                 "peak_source": "FP64 pipe: 2 lanes/clk/SM x 152 SMs x 2070 MHz x 2 flops (recipe nominal 1.25 TFLOP/s)",
                 "peak_measured": probe["tflops"], "frac_of_measured_peak": achieved_tflops / probe["tflops"],
-                "peak_measured_source": "%s, %d x %d threads x 8 chains x %d FMAs, best of 6, this run"
+                "peak_measured_source": "%s, %d x %d threads x 8 chains x %d FMAs, best of %d, this run"
                                         % (probe["kernel"], probe["launch"][0], probe["launch"][1],
-                                           probe["launch"][2]),
+                                           probe["launch"][2], probe["launches"]),
+                "peak_measured_median": probe["tflops_median"], "peak_measured_clocks": probe["clocks"],
                 "fp64_pipe_frac": instr_rate / peak_instr,
                 "hbm_gbs": hbm_gbs, "hbm_frac_of_measured": hbm_gbs / measured_hbm()}
 

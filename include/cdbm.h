@@ -300,6 +300,16 @@ cdbm_status cdbm_batch_autotune(cdbm_batch *b, int trial_steps, int *threads, in
 /* Sets the tile explicitly (threads 64, 128 or 256; blocks_per_sm 1..16). */
 cdbm_status cdbm_batch_set_tile(cdbm_batch *b, int threads, int blocks_per_sm);
 
+/* Enables (default) or disables the symmetric kernels.  When every tube starts with
+ * u_y = 0 (checked by cdbm_batch_init), each tube's state is mirror-symmetric in y --
+ * f_S = f_N, f_SE = f_NE, f_SW = f_NW -- and stays so, since the mirror images move
+ * alike along x and j_y = 0 gives them equal equilibria.  The symmetric kernels then
+ * compute the 10 distinct velocities only, drop the terms of j_y = 0, and write each
+ * result to both mirror planes; their results equal the general kernels' bit for bit
+ * (up to the sign of an exact zero).  Disabled, every batch runs the general
+ * kernels.  EINVAL for a NULL batch. */
+cdbm_status cdbm_batch_set_symmetric(cdbm_batch *b, int enable);
+
 /* rho, u_x, u_y, T of every cell ([total_cells] each, host or device, NULL skips).
  * Synchronous. */
 cdbm_status cdbm_batch_macros(cdbm_batch *b, double *rho, double *ux, double *uy, double *T);

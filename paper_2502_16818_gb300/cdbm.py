@@ -29,7 +29,7 @@ EXPORTS = ("cdbm_create", "cdbm_set_rk", "cdbm_init", "cdbm_step", "cdbm_set_sma
            "cdbm_set_row_marching", "cdbm_macros", "cdbm_tne", "cdbm_conserved_sums", "cdbm_get_state", "cdbm_set_state", "cdbm_state_ptr", "cdbm_time",
            "cdbm_sync", "cdbm_last_error", "cdbm_destroy", "cdbm_step_noalloc",
            "cdbm_batch_create", "cdbm_batch_init", "cdbm_batch_step", "cdbm_batch_autotune",
-           "cdbm_batch_set_tile", "cdbm_batch_macros", "cdbm_batch_info", "cdbm_batch_sync",
+           "cdbm_batch_set_tile", "cdbm_batch_set_symmetric", "cdbm_batch_macros", "cdbm_batch_info", "cdbm_batch_sync",
            "cdbm_batch_last_error", "cdbm_batch_destroy", "cdbm_adjoint_forward",
            "cdbm_adjoint_backward", "cdbm_adjoint_set_limiter", "cdbm_macros_vjp",
            "cdbm_diag_rcp64", "cdbm_diag_fp64_fma")
@@ -107,6 +107,7 @@ def load(path: str | None = None):
         "cdbm_batch_autotune": ([ctx, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "cdbm_batch_set_tile": ([ctx, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "cdbm_batch_set_symmetric": ([ctx, ctypes.c_int], ctypes.c_int),
         "cdbm_batch_macros": ([ctx, _vp, _vp, _vp, _vp], ctypes.c_int),
         "cdbm_batch_info": ([ctx, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -320,6 +321,11 @@ def cdbm_batch_set_tile(b, threads, blocks_per_sm):
     _bcheck(lib, b, lib.cdbm_batch_set_tile(b, int(threads), int(blocks_per_sm)))
 
 
+def cdbm_batch_set_symmetric(b, enable):
+    lib = load()
+    _bcheck(lib, b, lib.cdbm_batch_set_symmetric(b, int(bool(enable))))
+
+
 def cdbm_batch_macros(b, rho, ux, uy, T):
     lib = load()
     _bcheck(lib, b, lib.cdbm_batch_macros(b, rho, ux, uy, T))
@@ -511,6 +517,9 @@ class BatchSolver:
 
     def set_tile(self, threads, blocks_per_sm):
         cdbm_batch_set_tile(self.b, threads, blocks_per_sm)
+
+    def set_symmetric(self, enable):
+        cdbm_batch_set_symmetric(self.b, enable)
 
     def macros(self):
         """(rho, ux, uy, T) as concatenated float64 numpy arrays."""

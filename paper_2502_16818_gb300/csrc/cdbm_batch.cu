@@ -72,7 +72,24 @@ __device__ __forceinline__ TS pick(double d, float f)
 // arithmetic per cell is the flat (Ny = 1) stage of the single-grid kernels, with the
 // equilibrium in double or, with kDF, in df64.  Plain loads: the buffers are written
 // inside this kernel, so the read-only path may not be used.
-template <typename TS, int kStage, bool kDF>
+// With kSym the tube's state is y-symmetric (conserved_sym): only the 10 distinct
+// velocities are loaded and computed, each result is stored to its plane and to the
+// plane of its mirror image, and the equilibrium drops the terms of j_y = 0.  The
+// values are those of the general form.
+template <typename TS, bool kSym>
+__device__ __forceinline__ void load_state(const TS *g, long long P, int x, TS fs[kNV])
+{
+#pragma unroll
+    for (int i = 0; i < kNV; ++i)
+        if (!kSym || mirror_y(i) == i) fs[i] = g[i * P + x];
+    if constexpr (kSym) {
+#pragma unroll
+        for (int i = 0; i < kNV; ++i)
+            if (mirror_y(i) != i) fs[i] = fs[mirror_y(i)];
+    }
+}
+
+template <typename TS, int kStage, bool kDF, bool kSym = false>
 __device__ __forceinline__ void tube_stage(const TS *g, const TS *base, TS *out, long long P,
                                            const TubeInfo &t, const ClassConsts &C, TS a_self, TS a_base,
                                            unsigned *flag)
@@ -85,25 +102,32 @@ __device__ __forceinline__ void tube_stage(const TS *g, const TS *base, TS *out,
         const int xm2 = x >= 2 ? x - 2 : 0, xm1 = x >= 1 ? x - 1 : 0;
         const int xp1 = x + 1 < nx ? x + 1 : nx - 1, xp2 = x + 2 < nx ? x + 2 : nx - 1;
         TS fs[kNV];
-#pragma unroll
-        for (int i = 0; i < kNV; ++i) fs[i] = g[i * P + x];
+        load_state<TS, kSym>(g, P, x, fs);
         TS heq[kNV];
         if constexpr (kDF) {
             static_assert(kSingle<TS>, "df64 equilibrium is for the single-precision state");
-            df_equilibrium(C.dfeq[kStage], C.dfm, t.dfs[kStage], fs, heq, flag);
+            if constexpr (kSym) df_equilibrium_sym(C.dfeq[kStage], C.dfm, t.dfs[kStage], fs, heq, flag);
+            else df_equilibrium(C.dfeq[kStage], C.dfm, t.dfs[kStage], fs, heq, flag);
         } else {
             double f[kNV];
 #pragma unroll
             for (int i = 0; i < kNV; ++i) f[i] = widen(fs[i]);
-            const Prim s = primitives<kSingle<TS>>(f, C.m, t.rhoF, t.EF, flag);
             double h[kNV];
-            equilibrium<kSingle<TS>>(C.eq[kStage], C.m, s.q.rho, s.q.E, s.q.jx, s.q.jy, s.ux, s.uy, s.ru2,
-                                     s.jyuy, s.p, s.T, h, t.sF[kStage]);
+            if constexpr (kSym) {
+                const Prim s = primitives_sym<kSingle<TS>>(f, C.m, t.rhoF, t.EF, flag);
+                equilibrium_sym<kSingle<TS>>(C.eq[kStage], C.m, s.q.rho, s.q.E, s.q.jx, s.ux, s.ru2, s.p, s.T, h,
+                                             t.sF[kStage]);
+            } else {
+                const Prim s = primitives<kSingle<TS>>(f, C.m, t.rhoF, t.EF, flag);
+                equilibrium<kSingle<TS>>(C.eq[kStage], C.m, s.q.rho, s.q.E, s.q.jx, s.q.jy, s.ux, s.uy, s.ru2,
+                                         s.jyuy, s.p, s.T, h, t.sF[kStage]);
+            }
 #pragma unroll
             for (int i = 0; i < kNV; ++i) heq[i] = narrow<TS>(h[i]);
         }
 #pragma unroll
         for (int i = 0; i < kNV; ++i) {
+            if (kSym && mirror_y(i) != i) continue;
             TS o = fma_t(a_self, fs[i], heq[i]);
             if (kBase) o = fma_t(a_base, base[i * P + x], o);
             if (dirx(i) != 0) {
@@ -114,6 +138,7 @@ __device__ __forceinline__ void tube_stage(const TS *g, const TS *base, TS *out,
                 o = fma_t(-pick<TS>(lx[i >> 2], lx_f[i >> 2]), nnd(u2, u1, fs[i], d1), o);
             }
             out[i * P + x] = o;
+            if (kSym && sym_partner(i) >= 0) out[sym_partner(i) * P + x] = o;
         }
     }
 }
@@ -126,11 +151,13 @@ __device__ __forceinline__ void tube_stage(const TS *g, const TS *base, TS *out,
 // instructions per x term, with the operands and operations of nnd(), so the result
 // is the same bit for bit.  All threads run the same chunk loop and reach the block
 // barriers.
-template <int kStage, int kThreads>
+template <int kStage, int kThreads, bool kSym = false>
 __device__ __forceinline__ void tube_stage_shared_x(const double *g, const double *base, double *out, long long P,
                                                     const TubeInfo &t, const ClassConsts &C, double a_self,
                                                     double a_base, unsigned *flag, double (*row_u)[kThreads + 2])
 {
+    // with kSym the mirror images SW, SE (the x-moving ones) are skipped: 8 x terms
+    auto xterm = [](int i) { return dirx(i) != 0 && (!kSym || mirror_y(i) == i); };
     constexpr bool kBase = kStage == 1;
     const int nx = t.nx;
     const double *lx = t.lx[kStage];
@@ -144,18 +171,23 @@ __device__ __forceinline__ void tube_stage_shared_x(const double *g, const doubl
         const int xp1 = xc + 1 < nx ? xc + 1 : nx - 1, xp2 = xc + 2 < nx ? xc + 2 : nx - 1;
         double fs[kNV], o[kNV];
         if (active) {
-#pragma unroll
-            for (int i = 0; i < kNV; ++i) fs[i] = g[i * P + x];
-            const Prim s = primitives<false>(fs, C.m, 0.0, 0.0, flag);
+            load_state<double, kSym>(g, P, x, fs);
             double heq[kNV];
-            equilibrium<false>(C.eq[kStage], C.m, s.q.rho, s.q.E, s.q.jx, s.q.jy, s.ux, s.uy, s.ru2, s.jyuy, s.p,
-                               s.T, heq);
+            if constexpr (kSym) {
+                const Prim s = primitives_sym<false>(fs, C.m, 0.0, 0.0, flag);
+                equilibrium_sym<false>(C.eq[kStage], C.m, s.q.rho, s.q.E, s.q.jx, s.ux, s.ru2, s.p, s.T, heq);
+            } else {
+                const Prim s = primitives<false>(fs, C.m, 0.0, 0.0, flag);
+                equilibrium<false>(C.eq[kStage], C.m, s.q.rho, s.q.E, s.q.jx, s.q.jy, s.ux, s.uy, s.ru2, s.jyuy,
+                                   s.p, s.T, heq);
+            }
             int k = 0;
 #pragma unroll
             for (int i = 0; i < kNV; ++i) {
+                if (kSym && mirror_y(i) != i) continue;
                 o[i] = fma(a_self, fs[i], heq[i]);
                 if (kBase) o[i] = fma(a_base, base[i * P + x], o[i]);
-                if (dirx(i) != 0) {
+                if (xterm(i)) {
                     row_u[k][tid + 1] = fs[i] - g[i * P + (dirx(i) > 0 ? xm1 : xp1)];   // a of nnd()
                     ++k;
                 }
@@ -164,7 +196,7 @@ __device__ __forceinline__ void tube_stage_shared_x(const double *g, const doubl
                 int k2 = 0;
 #pragma unroll
                 for (int i = 0; i < kNV; ++i) {
-                    if (dirx(i) == 0) continue;
+                    if (!xterm(i)) continue;
                     const double *gp = g + i * P;
                     row_u[k2][0] = dirx(i) > 0 ? gp[xm1] - gp[xm2] : gp[xm1] - fs[i];
                     ++k2;
@@ -174,7 +206,7 @@ __device__ __forceinline__ void tube_stage_shared_x(const double *g, const doubl
                 int k2 = 0;
 #pragma unroll
                 for (int i = 0; i < kNV; ++i) {
-                    if (dirx(i) == 0) continue;
+                    if (!xterm(i)) continue;
                     const double *gp = g + i * P;
                     row_u[k2][last + 2] = dirx(i) > 0 ? gp[xp1] - fs[i] : gp[xp1] - gp[xp2];
                     ++k2;
@@ -186,7 +218,8 @@ __device__ __forceinline__ void tube_stage_shared_x(const double *g, const doubl
             int k = 0;
 #pragma unroll
             for (int i = 0; i < kNV; ++i) {
-                if (dirx(i) != 0) {
+                if (kSym && mirror_y(i) != i) continue;
+                if (xterm(i)) {
                     const int s = dirx(i);
                     const double av = row_u[k][tid + 1];          // c - u1
                     const double bv = row_u[k][tid + 1 + s];      // d1 - c
@@ -196,6 +229,7 @@ __device__ __forceinline__ void tube_stage_shared_x(const double *g, const doubl
                     ++k;
                 }
                 out[i * P + x] = o[i];
+                if (kSym && sym_partner(i) >= 0) out[sym_partner(i) * P + x] = o[i];
             }
         }
         __syncthreads();                              // the next chunk rewrites the buffer
@@ -207,7 +241,7 @@ __device__ __forceinline__ void tube_stage_shared_x(const double *g, const doubl
 // twice and stored once) and applies every operation of tube_stage<float, kStage,
 // true> to both with the packed FP32x2 instructions, so each cell gets the bits of
 // the one-cell form with about half the instruction issues.
-template <int kStage>
+template <int kStage, bool kSym = false>
 __device__ __forceinline__ void tube_stage2(const float *g, const float *base, float *out, long long P,
                                             const TubeInfo &t, const ClassConsts &C, float2 a_self,
                                             float2 a_base, unsigned *flag)
@@ -225,10 +259,19 @@ __device__ __forceinline__ void tube_stage2(const float *g, const float *base, f
         const int p1b = xb + 1 < nx ? xb + 1 : nx - 1, p2b = xb + 2 < nx ? xb + 2 : nx - 1;
         float2 fs[kNV], heq[kNV];
 #pragma unroll
-        for (int i = 0; i < kNV; ++i) fs[i] = make_float2(g[i * P + x], g[i * P + xb]);
-        df_equilibrium(C.dfeq2[kStage], C.dfm2, t.dfs2[kStage], fs, heq, flag);
+        for (int i = 0; i < kNV; ++i)
+            if (!kSym || mirror_y(i) == i) fs[i] = make_float2(g[i * P + x], g[i * P + xb]);
+        if constexpr (kSym) {
+#pragma unroll
+            for (int i = 0; i < kNV; ++i)
+                if (mirror_y(i) != i) fs[i] = fs[mirror_y(i)];
+            df_equilibrium_sym(C.dfeq2[kStage], C.dfm2, t.dfs2[kStage], fs, heq, flag);
+        } else {
+            df_equilibrium(C.dfeq2[kStage], C.dfm2, t.dfs2[kStage], fs, heq, flag);
+        }
 #pragma unroll
         for (int i = 0; i < kNV; ++i) {
+            if (kSym && mirror_y(i) != i) continue;
             float2 o = fma_rn(a_self, fs[i], heq[i]);
             if (kBase) o = fma_rn(a_base, make_float2(base[i * P + x], base[i * P + xb]), o);
             if (dirx(i) != 0) {
@@ -245,6 +288,10 @@ __device__ __forceinline__ void tube_stage2(const float *g, const float *base, f
             }
             out[i * P + x] = o.x;
             if (two) out[i * P + xb] = o.y;
+            if (kSym && sym_partner(i) >= 0) {
+                out[sym_partner(i) * P + x] = o.x;
+                if (two) out[sym_partner(i) * P + xb] = o.y;
+            }
         }
     }
 }
@@ -257,7 +304,7 @@ constexpr int batch_min_blocks(int threads, bool)
     return 384 / threads > 0 ? 384 / threads : 1;
 }
 
-template <typename TS, int kThreads, bool kDF>
+template <typename TS, int kThreads, bool kDF, bool kSym>
 __global__ void __launch_bounds__(kThreads, batch_min_blocks(kThreads, kDF)) batch_kernel(TS *f, TS *f1, const TubeInfo *tubes,
                                                          const int *work, const int *work_off, int nsteps,
                                                          const BatchArgs a, unsigned *flag)
@@ -273,17 +320,17 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks(kThreads, kDF)) bat
         TS *f1t = f1 + t.offset;
         for (int s = 0; s < nsteps; ++s) {
             if constexpr (!kSingle<TS>) {
-                tube_stage_shared_x<0, kThreads>(ft, nullptr, f1t, a.P, t, C, as0, ab0, flag, row_u);
+                tube_stage_shared_x<0, kThreads, kSym>(ft, nullptr, f1t, a.P, t, C, as0, ab0, flag, row_u);
                 __syncthreads();
-                tube_stage_shared_x<1, kThreads>(f1t, ft, ft, a.P, t, C, as1, ab1, flag, row_u);
+                tube_stage_shared_x<1, kThreads, kSym>(f1t, ft, ft, a.P, t, C, as1, ab1, flag, row_u);
             } else if constexpr (kDF) {
-                tube_stage2<0>(ft, nullptr, f1t, a.P, t, C, a.a_self_f2[0], a.a_base_f2[0], flag);
+                tube_stage2<0, kSym>(ft, nullptr, f1t, a.P, t, C, a.a_self_f2[0], a.a_base_f2[0], flag);
                 __syncthreads();
-                tube_stage2<1>(f1t, ft, ft, a.P, t, C, a.a_self_f2[1], a.a_base_f2[1], flag);
+                tube_stage2<1, kSym>(f1t, ft, ft, a.P, t, C, a.a_self_f2[1], a.a_base_f2[1], flag);
             } else {
-                tube_stage<TS, 0, kDF>(ft, nullptr, f1t, a.P, t, C, as0, ab0, flag);
+                tube_stage<TS, 0, kDF, kSym>(ft, nullptr, f1t, a.P, t, C, as0, ab0, flag);
                 __syncthreads();
-                tube_stage<TS, 1, kDF>(f1t, ft, ft, a.P, t, C, as1, ab1, flag);
+                tube_stage<TS, 1, kDF, kSym>(f1t, ft, ft, a.P, t, C, as1, ab1, flag);
             }
             __syncthreads();
         }
@@ -355,21 +402,24 @@ __global__ void __launch_bounds__(128) batch_macros_kernel(const BatchArgs a, co
     }
 }
 
-template <typename TS, bool kDF>
+template <typename TS, bool kDF, bool kSym>
 void *batch_func_t(int threads)
 {
     switch (threads) {
-    case 64: return (void *)batch_kernel<TS, 64, kDF>;
-    case 256: return (void *)batch_kernel<TS, 256, kDF>;
-    default: return (void *)batch_kernel<TS, 128, kDF>;
+    case 64: return (void *)batch_kernel<TS, 64, kDF, kSym>;
+    case 256: return (void *)batch_kernel<TS, 256, kDF, kSym>;
+    default: return (void *)batch_kernel<TS, 128, kDF, kSym>;
     }
 }
 
-void *batch_func(int precision, int threads)
+// sym: every tube's state is y-symmetric (u_y = 0 at initialisation)
+void *batch_func(int precision, int threads, bool sym)
 {
-    if (precision == CDBM_FP32_DF64) return batch_func_t<float, true>(threads);
-    if (precision == CDBM_FP32_BULK) return batch_func_t<float, false>(threads);
-    return batch_func_t<double, false>(threads);
+    if (precision == CDBM_FP32_DF64)
+        return sym ? batch_func_t<float, true, true>(threads) : batch_func_t<float, true, false>(threads);
+    if (precision == CDBM_FP32_BULK)
+        return sym ? batch_func_t<float, false, true>(threads) : batch_func_t<float, false, false>(threads);
+    return sym ? batch_func_t<double, false, true>(threads) : batch_func_t<double, false, false>(threads);
 }
 
 }  // namespace
@@ -398,6 +448,8 @@ struct cdbm_batch {
     double t;
     cudaGraphExec_t graph;
     int graph_steps;
+    bool sym;                          // every tube started with u_y = 0: y-symmetric states
+    bool sym_enabled;                  // use the symmetric kernels when sym (default)
     cdbm_status err;
     char msg[256];
 };
@@ -522,7 +574,7 @@ cdbm_status launch_run(cdbm_batch *b, int nsteps)
     const TubeInfo *tubes = b->d_tubes;
     const int *work = b->d_work, *off = b->d_work_off;
     void *args[] = {&f, &f1, (void *)&tubes, (void *)&work, (void *)&off, &nsteps, (void *)&b->args, &b->flag};
-    void *fn = batch_func(b->precision, b->threads);
+    void *fn = batch_func(b->precision, b->threads, b->sym && b->sym_enabled);
     return bcuda(b, cudaLaunchKernel(fn, dim3(b->blocks), dim3(b->threads), args, 0, b->stream), "batch launch");
 }
 
@@ -537,7 +589,7 @@ cdbm_status run_graph(cdbm_batch *b, int nsteps)
         void *args[] = {&f, &f1, (void *)&tubes, (void *)&work, (void *)&off, &nsteps, (void *)&b->args, &b->flag};
         cudaKernelNodeParams p;
         memset(&p, 0, sizeof(p));
-        p.func = batch_func(b->precision, b->threads);
+        p.func = batch_func(b->precision, b->threads, b->sym && b->sym_enabled);
         p.gridDim = dim3(b->blocks);
         p.blockDim = dim3(b->threads);
         p.kernelParams = args;
@@ -590,6 +642,8 @@ cdbm_status cdbm_batch_create(int ntubes, const int *nx, const double *dx, const
     b->user_alloc = allocator && allocator->alloc && allocator->free;
     if (b->user_alloc) b->alloc = *allocator;
     b->err = CDBM_OK;
+    b->sym = false;
+    b->sym_enabled = true;
     strcpy(b->msg, "no error");
     b->nx.assign(nx, nx + ntubes);
     b->offs.assign(ntubes + 1, 0);
@@ -714,6 +768,13 @@ cdbm_status cdbm_batch_init(cdbm_batch *b, const double *rho, const double *ux, 
             dev[k] = stage + k * n;
         }
     }
+    // u_y = 0 everywhere: every tube's state is y-symmetric and stays so
+    bool sym = true;
+    for (size_t c = 0; c < n && sym; ++c) sym = host[2][c] == 0.0;
+    if (sym != b->sym) {
+        b->sym = sym;
+        drop_batch_graph(b);
+    }
     // per-tube reference state (FP32-bulk): means of rho and T over the tube
     for (int t = 0; t < b->ntubes; ++t) {
         TubeInfo &ti = b->info[t];
@@ -828,6 +889,17 @@ cdbm_status cdbm_batch_set_tile(cdbm_batch *b, int threads, int blocks_per_sm)
     if ((threads != 64 && threads != 128 && threads != 256) || blocks_per_sm < 1 || blocks_per_sm > 16)
         return bset_err(b, CDBM_EINVAL, "tile: threads must be 64, 128 or 256 and blocks_per_sm in 1..16");
     return set_tile(b, threads, blocks_per_sm);
+}
+
+cdbm_status cdbm_batch_set_symmetric(cdbm_batch *b, int enable)
+{
+    if (!b) return CDBM_EINVAL;
+    if (b->err) return b->err;
+    if ((enable != 0) != b->sym_enabled) {
+        b->sym_enabled = enable != 0;
+        drop_batch_graph(b);
+    }
+    return CDBM_OK;
 }
 
 cdbm_status cdbm_batch_macros(cdbm_batch *b, double *rho, double *ux, double *uy, double *T)

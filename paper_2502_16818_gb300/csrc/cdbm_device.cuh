@@ -260,6 +260,125 @@ __device__ __forceinline__ Prim primitives(const double f[kNV], const ModelConst
     return s;
 }
 
+// ---- y-symmetric states of 1-D grids ----
+// On a 1-D grid (ny = 1) a state that is mirror-symmetric in y -- f_S = f_N in the
+// axis groups, f_SE = f_NE and f_SW = f_NW in the diagonal ones, in every cell --
+// stays so under the step: the mirror images have equal x components, so their
+// transport is the same, and with j_y = 0 the equilibrium gives them equal values.
+// Every initial state with u_y = 0 is such a state (f_eq of u_y = 0 is symmetric).
+// There j_y = u_y = 0 exactly, and the *_sym forms below drop every term that then
+// vanishes: they return, value for value, what the general forms return on the
+// same state (up to the sign of an exact zero).  Only 10 of the 16 velocities are
+// distinct.
+constexpr int kNSym = 10;
+__host__ __device__ constexpr int sym_vel(int k)      // k-th distinct velocity: E N W | NE NW per group pair
+{
+    return k < 3 ? k : (k < 5 ? k + 1 : (k < 8 ? k + 3 : k + 4));
+}
+__host__ __device__ constexpr int mirror_y(int i)     // the velocity whose value i holds on a symmetric state
+{
+    return (i & 3) == 3 && ((i >> 2) & 1) == 0 ? i - 2              // S -> N
+           : ((i >> 2) & 1) == 1 && (i & 3) == 2 ? i - 1           // SW -> NW
+           : ((i >> 2) & 1) == 1 && (i & 3) == 3 ? i - 3           // SE -> NE
+           : i;
+}
+
+__host__ __device__ constexpr int sym_partner(int i)  // the mirror image a distinct velocity stands for, or -1
+{
+    return ((i >> 2) & 1) == 0 ? ((i & 3) == 1 ? i + 2 : -1)  // N -> S
+                               : ((i & 3) == 0 ? i + 3 : ((i & 3) == 1 ? i + 1 : -1));   // NE -> SE, NW -> SW
+}
+
+// conserved() on a symmetric state (j_y = 0).
+__device__ __forceinline__ Cons conserved_sym(const double f[kNV], const ModelConsts &m)
+{
+    double s0[4], sx[4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const double *q = f + 4 * g;
+        if ((g & 1) == 0) {
+            sx[g] = q[0] - q[2];
+            s0[g] = (q[0] + q[2]) + (q[1] + q[3]);
+        } else {
+            const double e = q[0] + q[3], w = q[1] + q[2];
+            sx[g] = e - w;
+            s0[g] = e + w;
+        }
+    }
+    Cons r;
+    r.rho = (s0[0] + s0[1]) + (s0[2] + s0[3]);
+    r.jx = fma(m.c[3], sx[3], fma(m.c[2], sx[2], fma(m.c[1], sx[1], m.c[0] * sx[0])));
+    r.jy = 0.0;
+    r.E = fma(m.w[3], s0[3], fma(m.w[2], s0[2], fma(m.w[1], s0[1], m.w[0] * s0[0])));
+    return r;
+}
+
+// primitives<kShift>() on a symmetric state (u_y = 0, rho u^2 = j_x u_x).
+template <bool kShift>
+__device__ __forceinline__ Prim primitives_sym(const double f[kNV], const ModelConsts &m, double rhoF, double EF,
+                                               unsigned *flag)
+{
+    Prim s;
+    s.q = conserved_sym(f, m);
+    if (kShift) {
+        s.q.rho += rhoF;
+        s.q.E += EF;
+    }
+    const double r = rcp64(s.q.rho);
+    s.r = r;
+    s.ux = s.q.jx * r;
+    s.uy = 0.0;
+    s.jyuy = 0.0;
+    s.ru2 = __dmul_rn(s.q.jx, s.ux);     // the general fma(j_x, u_x, +0), never contracted
+    s.p = (s.q.E - s.ru2) * m.invK;
+    s.T = s.p * r;
+    if (!(positive_finite(s.q.rho) && positive_finite(s.p))) atomicOr(flag, kFlagNonPhys);
+    return s;
+}
+
+// equilibrium<kShift>() on a symmetric state: u_y = j_y = 0, so rho u^2 = m5 - m7 =
+// j_x u_x, m6 = m15 = 0 (no diagonal quadrupole), u^2 = u_x^2 - u_y^2 = u_x^2, and
+// the y-odd members equal their mirror images.  out receives all 16 values.
+template <bool kShift = false>
+__device__ __forceinline__ void equilibrium_sym(const EqBlocks &B, const ModelConsts &m, double rho, double E,
+                                                double jx, double ux, double ru2, double P, double T,
+                                                double out[kNV], const double *s0_shift = nullptr)
+{
+    const double u2 = ux * ux;
+    const double m1416 = fma(T, fma(m.Kp6, ru2, m.twoKp2 * P), ru2 * u2);
+    const double W4 = fma(m.Kp4, T, u2);
+    const double d57 = ru2;
+    double s0[4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const double *S = B.S + 4 * g;
+        if (kShift)
+            s0[g] = fma(S[3], m1416, fma(S[2], ru2, fma(S[1], E, fma(S[0], rho, -s0_shift[g]))));
+        else
+            s0[g] = fma(S[3], m1416, fma(S[2], ru2, fma(S[1], E, S[0] * rho)));
+    }
+    const double dq[2] = {d57 * fma(B.B1[1], W4, B.B1[0]), d57 * fma(B.B1[3], W4, B.B1[2])};
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const double *W = B.Vc + 4 * g;
+        const double px = fma(W[3], u2, fma(W[2], u2, fma(W[1], T, W[0])));
+        double *o = out + 4 * g;
+        if ((g & 1) == 0) {
+            const double A = s0[g] + dq[g >> 1], Bv = s0[g] - dq[g >> 1];
+            o[0] = fma(jx, px, A);
+            o[2] = fma(-jx, px, A);
+            o[1] = Bv;
+            o[3] = Bv;
+        } else {
+            const double U = __dmul_rn(jx, px);   // the general fma(j_x, px, +-0)
+            o[0] = s0[g] + U;
+            o[3] = o[0];
+            o[1] = s0[g] - U;
+            o[2] = o[1];
+        }
+    }
+}
+
 // Neighbour index along an axis of n cells: periodic wrap or zero-gradient clamp.
 __device__ __forceinline__ int neighbour(int j, int n, int bc)
 {

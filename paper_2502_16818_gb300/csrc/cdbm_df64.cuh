@@ -9,13 +9,15 @@
 // Error model.  Every quantity of the stage equilibrium is at most of the size of
 // the reference equilibrium F (the moments of f, their products with O(1) block
 // coefficients), and what must be accurate is the *absolute* error, against the
-// single-precision deviation g = f - F the result is rounded to.  So the sums use
-// the cheap ("sloppy") double-float addition, whose error is a few 2^-48 of its
-// operands rather than of its result, and products are left unnormalised (the low
-// part may reach a few ulp of the high part); both keep the absolute error of every
-// quantity at a few 2^-47 of F, i.e. below 1/100 ulp of any deviation larger than
-// about 2^-17 F.  Cancellation against F is harmless under this model: it only
-// makes the final rounding to float relative to the smaller deviation.
+// single-precision deviation g = f - F the result is rounded to.  So the sums add
+// the high parts exactly and the low parts in float and leave the pair unnormalised
+// (df_add_q), with an error of a few 2^-48 of the operands rather than of the result,
+// and products are left unnormalised too (the low part may reach a few ulp of the
+// high part); both keep the absolute error of every quantity at a few 2^-47 of F,
+// i.e. below 1/100 ulp of any deviation larger than about 2^-17 F.  Only the density
+// is renormalised, because its reciprocal starts from the high part.  Cancellation
+// against F is harmless under this model: it only makes the final rounding to float
+// relative to the smaller deviation.
 //
 // On GB300 the FP64 pipe runs 1/64 of the FP32 rate, so moving the equilibrium of
 // the single-precision state from double to double-float trades each FP64
@@ -97,6 +99,28 @@ __device__ __forceinline__ dfl<L> df_neg(dfl<L> x) { return {neg(x.hi), neg(x.lo
 template <typename L>
 __device__ __forceinline__ dfl<L> df_sub(dfl<L> x, dfl<L> y) { return df_add(x, df_neg(y)); }
 
+// x + y without the final renormalisation of df_add: the exact sum of the high parts
+// and, in float, the low parts plus its rounding error.  The pair is left
+// unnormalised: its low part may exceed half an ulp of the high part (by the low
+// parts of the operands and, after cancellation, by more).  Under the absolute error
+// model that costs nothing where the result feeds further sums, products or the final
+// rounding to float: each of those forms the high parts exactly and carries the low
+// parts as float terms whose rounding is 2^-24 of their own size, i.e. a few 2^-48 of
+// the operands.  Only the reciprocal, which starts from the high part, takes a
+// normalised operand (df_norm).
+template <typename L>
+__device__ __forceinline__ dfl<L> df_add_q(dfl<L> x, dfl<L> y)
+{
+    const dfl<L> s = two_sum(x.hi, y.hi);
+    return {s.hi, add_rn(add_rn(x.lo, y.lo), s.lo)};
+}
+template <typename L>
+__device__ __forceinline__ dfl<L> df_sub_q(dfl<L> x, dfl<L> y) { return df_add_q(x, df_neg(y)); }
+
+// The pair renormalised (|lo| <= half an ulp of hi).
+template <typename L>
+__device__ __forceinline__ dfl<L> df_norm(dfl<L> x) { return fast_two_sum(x.hi, x.lo); }
+
 // x * y, unnormalised: the exact error of hi * hi plus the cross terms (x.lo * y.lo
 // is below the df rounding and dropped).
 template <typename L>
@@ -111,6 +135,16 @@ __device__ __forceinline__ dfl<L> df_mul(dfl<L> x, dfl<L> y)
 
 template <typename L>
 __device__ __forceinline__ dfl<L> df_fma(dfl<L> a, dfl<L> b, dfl<L> c) { return df_add(df_mul(a, b), c); }
+template <typename L>
+__device__ __forceinline__ dfl<L> df_fma_q(dfl<L> a, dfl<L> b, dfl<L> c) { return df_add_q(df_mul(a, b), c); }
+
+// x * r for a plain float r: the exact error of hi * r plus lo * r.
+template <typename L>
+__device__ __forceinline__ dfl<L> df_mul1(dfl<L> x, L r)
+{
+    const L p = mul_rn(x.hi, r);
+    return {p, fma_rn(x.lo, r, fma_rn(x.hi, r, neg(p)))};
+}
 
 __device__ __forceinline__ float rcp_estimate(float x)
 {
@@ -120,16 +154,17 @@ __device__ __forceinline__ float rcp_estimate(float x)
 }
 __device__ __forceinline__ float2 rcp_estimate(float2 x) { return make_float2(rcp_estimate(x.x), rcp_estimate(x.y)); }
 
-// 1 / x: hardware float estimate (about 2^-23 relative) refined by one Newton step
-// in df64, r + r (1 - x r), which squares the relative error.
+// 1 / x for a normalised x: hardware float estimate r (about 2^-23 relative)
+// refined by one Newton step in df64, r + r (1 - x r), which squares the relative
+// error.  The result is left unnormalised.
 template <typename L>
 __device__ __forceinline__ dfl<L> df_rcp(dfl<L> x)
 {
-    const dfl<L> r = df_of(rcp_estimate(x.hi));
+    const L r = rcp_estimate(x.hi);
     L one;
     if constexpr (std::is_same<L, float>::value) one = 1.0f; else one = make_float2(1.0f, 1.0f);
-    const dfl<L> e = df_sub(df_of(one), df_mul(x, r));
-    return df_add(r, df_mul(r, e));
+    const dfl<L> e = df_sub_q(df_of(one), df_mul1(x, r));
+    return df_add_q(df_of(r), df_mul1(e, r));
 }
 
 // true iff v > 0 and finite (bit tests), in every lane.
@@ -172,14 +207,14 @@ template <typename L>
 __device__ __forceinline__ void df_group_components(int g, const L q[4], dfl<L> &s0, dfl<L> &sx, dfl<L> &sy)
 {
     if ((g & 1) == 0) {
-        s0 = df_add(two_sum(q[0], q[2]), two_sum(q[1], q[3]));
+        s0 = df_add_q(two_sum(q[0], q[2]), two_sum(q[1], q[3]));
         sx = two_sum(q[0], neg(q[2]));
         sy = two_sum(q[1], neg(q[3]));
     } else {
         const dfl<L> e = two_sum(q[0], q[3]), w = two_sum(q[1], q[2]);
-        sx = df_sub(e, w);
-        sy = df_sub(two_sum(q[0], q[1]), two_sum(q[2], q[3]));
-        s0 = df_add(e, w);
+        sx = df_sub_q(e, w);
+        sy = df_sub_q(two_sum(q[0], q[1]), two_sum(q[2], q[3]));
+        s0 = df_add_q(e, w);
     }
 }
 
@@ -190,35 +225,38 @@ struct DFScalars {
 
 // Moments, primitives and raw-moment factors from the group components of all four
 // groups (the steps of primitives() and the shared part of equilibrium<true>()).
+// With j u_x and j_y u_y formed once, rho u^2 and m5 - m7 are their sum and
+// difference, and u^2 = rho u^2 / rho, u_x^2 - u_y^2 = (m5 - m7) / rho.  Only rho,
+// the operand of the reciprocal, is renormalised.
 template <typename L>
 __device__ __forceinline__ DFScalars<L> df_scalars(const DFModelT<L> &d, const DFShiftT<L> &R, const dfl<L> s0[4],
                                                    const dfl<L> sx[4], const dfl<L> sy[4], unsigned *flag)
 {
     DFScalars<L> c;
-    c.rho = df_add(df_add(df_add(s0[0], s0[1]), df_add(s0[2], s0[3])), R.rhoF);
+    c.rho = df_norm(df_add_q(df_add_q(df_add_q(s0[0], s0[1]), df_add_q(s0[2], s0[3])), R.rhoF));
     c.jx = df_mul(d.c[0], sx[0]);
     c.jy = df_mul(d.c[0], sy[0]);
-    c.E = df_add(df_mul(d.w[0], s0[0]), R.EF);
+    c.E = df_add_q(df_mul(d.w[0], s0[0]), R.EF);
 #pragma unroll
     for (int g = 1; g < 4; ++g) {
-        c.jx = df_fma(d.c[g], sx[g], c.jx);
-        c.jy = df_fma(d.c[g], sy[g], c.jy);
-        c.E = df_fma(d.w[g], s0[g], c.E);
+        c.jx = df_fma_q(d.c[g], sx[g], c.jx);
+        c.jy = df_fma_q(d.c[g], sy[g], c.jy);
+        c.E = df_fma_q(d.w[g], s0[g], c.E);
     }
     c.r = df_rcp(c.rho);
     c.ux = df_mul(c.jx, c.r);
     c.uy = df_mul(c.jy, c.r);
+    const dfl<L> jxux = df_mul(c.jx, c.ux);
     c.jyuy = df_mul(c.jy, c.uy);
-    c.ru2 = df_fma(c.jx, c.ux, c.jyuy);
-    c.P = df_mul(df_sub(c.E, c.ru2), d.invK);
+    c.ru2 = df_add_q(jxux, c.jyuy);
+    c.d57 = df_sub_q(jxux, c.jyuy);
+    c.P = df_mul(df_sub_q(c.E, c.ru2), d.invK);
     c.T = df_mul(c.P, c.r);
     if (flag && !(positive_finite_f(c.rho.hi) && positive_finite_f(c.P.hi))) atomicOr(flag, kFlagNonPhys);
-    const dfl<L> ux2 = df_mul(c.ux, c.ux), uy2 = df_mul(c.uy, c.uy);
-    c.u2 = df_add(ux2, uy2);
-    c.du2 = df_sub(ux2, uy2);
-    c.m1416 = df_fma(c.T, df_fma(d.Kp6, c.ru2, df_mul(d.twoKp2, c.P)), df_mul(c.ru2, c.u2));
-    c.W4 = df_fma(d.Kp4, c.T, c.u2);
-    c.d57 = df_sub(df_mul(c.jx, c.ux), c.jyuy);
+    c.u2 = df_mul(c.ru2, c.r);
+    c.du2 = df_mul(c.d57, c.r);
+    c.m1416 = df_fma_q(c.T, df_fma_q(d.Kp6, c.ru2, df_mul(d.twoKp2, c.P)), df_mul(c.ru2, c.u2));
+    c.W4 = df_fma_q(d.Kp4, c.T, c.u2);
     c.m6 = df_mul(c.jx, c.uy);
     return c;
 }
@@ -229,21 +267,108 @@ __device__ __forceinline__ void df_group_equilibrium(int g, const DFBlocksT<L> &
                                                      const DFScalars<L> &c, L heq[4])
 {
     const dfl<L> *S = B.S + 4 * g;
-    const dfl<L> s = df_fma(S[3], c.m1416, df_fma(S[2], c.ru2, df_fma(S[1], c.E, df_mul(S[0], c.rho))));
-    const L c0 = df_to_float(df_sub(s, R.sF[g]));
+    const dfl<L> s = df_fma_q(S[3], c.m1416, df_fma_q(S[2], c.ru2, df_fma_q(S[1], c.E, df_mul(S[0], c.rho))));
+    const L c0 = df_to_float(df_sub_q(s, R.sF[g]));
     // V0 + V1 u_x^2 + V2 u_y^2 + V3 T and its mirror, through the shared part
     // V0 + V3 T + (V1 + V2)/2 u^2 and the odd part (V1 - V2)/2 (u_x^2 - u_y^2)
-    const dfl<L> cm = df_fma(B.Vs[g], c.u2, df_fma(B.V3[g], c.T, B.V0[g]));
+    const dfl<L> cm = df_fma_q(B.Vs[g], c.u2, df_fma_q(B.V3[g], c.T, B.V0[g]));
     const dfl<L> cd = df_mul(B.Vd[g], c.du2);
-    const L cx = df_to_float(df_mul(c.jx, df_add(cm, cd)));
-    const L cy = df_to_float(df_mul(c.jy, df_sub(cm, cd)));
+    const L cx = df_to_float(df_mul(c.jx, df_add_q(cm, cd)));
+    const L cy = df_to_float(df_mul(c.jy, df_sub_q(cm, cd)));
     if ((g & 1) == 0) {                 // g = 0: a, g = 2: c
-        const L dq = df_to_float(df_mul(c.d57, df_fma(B.B1[g + 1], c.W4, B.B1[g])));
+        const L dq = df_to_float(df_mul(c.d57, df_fma_q(B.B1[g + 1], c.W4, B.B1[g])));
         rebuild_axis_f(heq, c0, dq, cx, cy);
     } else {                            // g = 1: b, g = 3: d
-        const L q = df_to_float(df_mul(c.m6, df_fma(B.B2[g], c.W4, B.B2[g - 1])));
+        const L q = df_to_float(df_mul(c.m6, df_fma_q(B.B2[g], c.W4, B.B2[g - 1])));
         rebuild_diag_f(heq, c0, q, cx, cy);
     }
+}
+
+// ---- the same on a y-symmetric 1-D state (see conserved_sym): j_y = u_y = 0 ----
+
+// Group components without the y-odd one.
+template <typename L>
+__device__ __forceinline__ void df_group_components_sym(int g, const L q[4], dfl<L> &s0, dfl<L> &sx)
+{
+    if ((g & 1) == 0) {
+        s0 = df_add_q(two_sum(q[0], q[2]), two_sum(q[1], q[3]));
+        sx = two_sum(q[0], neg(q[2]));
+    } else {
+        const dfl<L> e = two_sum(q[0], q[3]), w = two_sum(q[1], q[2]);
+        sx = df_sub_q(e, w);
+        s0 = df_add_q(e, w);
+    }
+}
+
+// df_scalars with j_y = u_y = 0: rho u^2 = m5 - m7 = j_x u_x and u_x^2 - u_y^2 = u^2;
+// the fields of j_y, u_y, j_y u_y and m6 are left unset.
+template <typename L>
+__device__ __forceinline__ DFScalars<L> df_scalars_sym(const DFModelT<L> &d, const DFShiftT<L> &R,
+                                                       const dfl<L> s0[4], const dfl<L> sx[4], unsigned *flag)
+{
+    DFScalars<L> c;
+    c.rho = df_norm(df_add_q(df_add_q(df_add_q(s0[0], s0[1]), df_add_q(s0[2], s0[3])), R.rhoF));
+    c.jx = df_mul(d.c[0], sx[0]);
+    c.E = df_add_q(df_mul(d.w[0], s0[0]), R.EF);
+#pragma unroll
+    for (int g = 1; g < 4; ++g) {
+        c.jx = df_fma_q(d.c[g], sx[g], c.jx);
+        c.E = df_fma_q(d.w[g], s0[g], c.E);
+    }
+    c.r = df_rcp(c.rho);
+    c.ux = df_mul(c.jx, c.r);
+    c.ru2 = df_mul(c.jx, c.ux);
+    c.d57 = c.ru2;
+    c.P = df_mul(df_sub_q(c.E, c.ru2), d.invK);
+    c.T = df_mul(c.P, c.r);
+    if (flag && !(positive_finite_f(c.rho.hi) && positive_finite_f(c.P.hi))) atomicOr(flag, kFlagNonPhys);
+    c.u2 = df_mul(c.ru2, c.r);
+    c.du2 = c.u2;
+    c.m1416 = df_fma_q(c.T, df_fma_q(d.Kp6, c.ru2, df_mul(d.twoKp2, c.P)), df_mul(c.ru2, c.u2));
+    c.W4 = df_fma_q(d.Kp4, c.T, c.u2);
+    return c;
+}
+
+// df_group_equilibrium on a symmetric state: no y-odd part, no diagonal quadrupole;
+// heq receives all four members.
+template <typename L>
+__device__ __forceinline__ void df_group_equilibrium_sym(int g, const DFBlocksT<L> &B, const DFShiftT<L> &R,
+                                                         const DFScalars<L> &c, L heq[4])
+{
+    const dfl<L> *S = B.S + 4 * g;
+    const dfl<L> s = df_fma_q(S[3], c.m1416, df_fma_q(S[2], c.ru2, df_fma_q(S[1], c.E, df_mul(S[0], c.rho))));
+    const L c0 = df_to_float(df_sub_q(s, R.sF[g]));
+    const dfl<L> cm = df_fma_q(B.Vs[g], c.u2, df_fma_q(B.V3[g], c.T, B.V0[g]));
+    const dfl<L> cd = df_mul(B.Vd[g], c.du2);
+    const L cx = df_to_float(df_mul(c.jx, df_add_q(cm, cd)));
+    if ((g & 1) == 0) {
+        const L dq = df_to_float(df_mul(c.d57, df_fma_q(B.B1[g + 1], c.W4, B.B1[g])));
+        const L A = add_rn(c0, dq), Bv = sub_rn(c0, dq);
+        heq[0] = add_rn(A, cx);
+        heq[2] = sub_rn(A, cx);
+        heq[1] = Bv;
+        heq[3] = Bv;
+    } else {
+        heq[0] = add_rn(c0, cx);
+        heq[3] = heq[0];
+        heq[1] = sub_rn(c0, cx);
+        heq[2] = heq[1];
+    }
+}
+
+// df_equilibrium on a symmetric state (all 16 values; fs holds all 16, the mirror
+// images equal).
+template <typename L>
+__device__ __forceinline__ void df_equilibrium_sym(const DFBlocksT<L> &B, const DFModelT<L> &d,
+                                                   const DFShiftT<L> &R, const L fs[kNV], L heq[kNV],
+                                                   unsigned *flag)
+{
+    dfl<L> s0[4], sx[4];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) df_group_components_sym(g, fs + 4 * g, s0[g], sx[g]);
+    const DFScalars<L> c = df_scalars_sym(d, R, s0, sx, flag);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) df_group_equilibrium_sym(g, B, R, c, heq + 4 * g);
 }
 
 // Scaled equilibrium deviation of one cell (or, with L = float2, of two cells) of

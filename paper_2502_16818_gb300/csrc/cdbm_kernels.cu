@@ -307,7 +307,10 @@ __global__ void __launch_bounds__(kStageThreads, stage_min_blocks(kDF))
 // which its y transport reads after the equilibrium and which is the state of the
 // next row.  Each thread copies and reads only its own two columns, so the copies
 // need the thread's own wait only, no block barrier.
-constexpr int kMarch2MinBlocks = 3;
+#ifndef CDBM_MARCH2_MIN_BLOCKS
+#define CDBM_MARCH2_MIN_BLOCKS 3
+#endif
+constexpr int kMarch2MinBlocks = CDBM_MARCH2_MIN_BLOCKS;
 // Rows staged ahead by cp.async: two buffers of [kNV][kStageThreads] float2.
 constexpr size_t kMarch2StageBytes = 2 * kNV * kStageThreads * sizeof(float2);
 
@@ -355,6 +358,18 @@ __global__ void __launch_bounds__(kStageThreads, kMarch2MinBlocks)
         else return make_float2(__ldg(p + x0), __ldg(p + x1));
     };
     auto ld_at = [&](const float *p, int ca, int cb) -> float2 { return make_float2(__ldg(p + ca), __ldg(p + cb)); };
+    // The x neighbours of the pair outside it are (x0 - 2, x0 - 1) and (x0 + 2, x0 + 3).
+    // With nx even each of those is an aligned pair of one row wherever the boundary
+    // maps it onto two neighbouring columns (always for periodic edges), and moves as
+    // one 8-byte load; otherwise (a clamped edge) as two 4-byte loads.
+    const bool pairL = kVec && m1a == m2a + 1 && (m2a & 1) == 0;
+    const bool pairR = kVec && p2b == p2a + 1 && (p2a & 1) == 0;
+    auto ld_left = [&](const float *p) -> float2 {
+        return pairL ? __ldg(reinterpret_cast<const float2 *>(p + m2a)) : make_float2(__ldg(p + m2a), __ldg(p + m1a));
+    };
+    auto ld_right = [&](const float *p) -> float2 {
+        return pairR ? __ldg(reinterpret_cast<const float2 *>(p + p2a)) : make_float2(__ldg(p + p2a), __ldg(p + p2b));
+    };
     auto stage_row = [&](int b, size_t row) {       // the thread's two cells of a row, all planes
 #pragma unroll
         for (int i = 0; i < kNV; ++i) {
@@ -414,9 +429,18 @@ __global__ void __launch_bounds__(kStageThreads, kMarch2MinBlocks)
             if (dirx(i) != 0) {
                 const float *gp = g + i * P + row;
                 const bool pos = dirx(i) > 0;
-                const float2 u2 = pos ? ld_at(gp, m2a, m2b) : ld_at(gp, p2a, p2b);
-                const float2 u1 = pos ? ld_at(gp, m1a, m1b) : ld_at(gp, p1a, p1b);
-                const float2 d1 = pos ? ld_at(gp, p1a, p1b) : ld_at(gp, m1a, m1b);
+                float2 u2, u1, d1;
+                if constexpr (kVec) {
+                    // the pair's own cells stand in for the neighbours inside the pair
+                    const float2 L = ld_left(gp), Rr = ld_right(gp);
+                    u2 = pos ? L : Rr;
+                    u1 = pos ? make_float2(L.y, fs[i].x) : make_float2(fs[i].y, Rr.x);
+                    d1 = pos ? make_float2(fs[i].y, Rr.x) : make_float2(L.y, fs[i].x);
+                } else {
+                    u2 = pos ? ld_at(gp, m2a, m2b) : ld_at(gp, p2a, p2b);
+                    u1 = pos ? ld_at(gp, m1a, m1b) : ld_at(gp, p1a, p1b);
+                    d1 = pos ? ld_at(gp, p1a, p1b) : ld_at(gp, m1a, m1b);
+                }
                 const float2 av = sub_rn(fs[i], u1);
                 const float2 bv = sub_rn(d1, fs[i]);
                 const float2 ev = sub_rn(u1, u2);

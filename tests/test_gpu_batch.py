@@ -89,6 +89,41 @@ def test_batch_result_independent_of_tile(precision):
             assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_batch_symmetric_kernels_equal_general_kernels(precision):
+    """Tubes that start with u_y = 0 stay mirror-symmetric in y; the symmetric
+    kernels compute the 10 distinct velocities only and must give the general
+    kernels' result bit for bit."""
+    from paper_2502_16818_gb300 import BatchSolver
+    tubes = tubes_small(n=20, seed=7, steps=60)
+    outs = []
+    for sym in (True, False):
+        b = BatchSolver(tubes, precision=precision)
+        b.init(tubes)
+        b.set_symmetric(sym)
+        b.step(60)
+        b.sync()
+        outs.append(b.macros())
+        b.close()
+    for a, c in zip(*outs):
+        assert np.array_equal(a, c)
+
+
+def test_batch_with_transverse_velocity_uses_general_kernels():
+    """A tube with u_y != 0 is not symmetric: the batch runs the general kernels,
+    and each tube still matches the oracle."""
+    tubes = tubes_small(n=5, seed=8, steps=80)
+    tubes[2].uy = np.full_like(tubes[2].uy, 0.05)
+    b, out = run_batch(tubes, 80)
+    for t, w in enumerate(tubes):
+        got = b.tube(out, t)
+        ref = oracle_tube(w, 80)
+        us = max(np.abs(ref[1]).max(), np.abs(ref[2]).max(), 1e-300)
+        du = max(np.abs(got[1] - ref[1][0]).max(), np.abs(got[2] - ref[2][0]).max()) / us
+        assert rel(got[0], ref[0][0]) <= 1e-10 and du <= 1e-10 and rel(got[3], ref[3][0]) <= 1e-10, t
+    assert np.abs(b.tube(out, 2)[2]).max() > 0.01
+
+
 def test_batch_matches_single_grid_path():
     """Each tube of an FP64 batch equals the same tube run alone with one launch per
     stage, bit for bit: both use the same per-cell operations.  (The single-grid
