@@ -223,26 +223,29 @@ struct DFScalars {
     dfl<L> rho, E, jx, jy, r, ux, uy, jyuy, ru2, P, T, u2, du2, m1416, W4, d57, m6;
 };
 
-// Moments, primitives and raw-moment factors from the group components of all four
-// groups (the steps of primitives() and the shared part of equilibrium<true>()).
-// With j u_x and j_y u_y formed once, rho u^2 and m5 - m7 are their sum and
-// difference, and u^2 = rho u^2 / rho, u_x^2 - u_y^2 = (m5 - m7) / rho.  Only rho,
-// the operand of the reciprocal, is renormalised.
+// Conserved moments from the group components of all four groups.  Every sum over
+// the groups is taken pairwise, (a + b) + (c + d): two independent chains instead of
+// one of three dependent double-float additions.
 template <typename L>
-__device__ __forceinline__ DFScalars<L> df_scalars(const DFModelT<L> &d, const DFShiftT<L> &R, const dfl<L> s0[4],
-                                                   const dfl<L> sx[4], const dfl<L> sy[4], unsigned *flag)
+__device__ __forceinline__ void df_sums(const DFModelT<L> &d, const DFShiftT<L> &R, const dfl<L> s0[4],
+                                        const dfl<L> sx[4], const dfl<L> sy[4], DFScalars<L> &c)
 {
-    DFScalars<L> c;
     c.rho = df_norm(df_add_q(df_add_q(df_add_q(s0[0], s0[1]), df_add_q(s0[2], s0[3])), R.rhoF));
-    c.jx = df_mul(d.c[0], sx[0]);
-    c.jy = df_mul(d.c[0], sy[0]);
-    c.E = df_add_q(df_mul(d.w[0], s0[0]), R.EF);
-#pragma unroll
-    for (int g = 1; g < 4; ++g) {
-        c.jx = df_fma_q(d.c[g], sx[g], c.jx);
-        c.jy = df_fma_q(d.c[g], sy[g], c.jy);
-        c.E = df_fma_q(d.w[g], s0[g], c.E);
-    }
+    c.jx = df_add_q(df_fma_q(d.c[1], sx[1], df_mul(d.c[0], sx[0])), df_fma_q(d.c[3], sx[3], df_mul(d.c[2], sx[2])));
+    c.jy = df_add_q(df_fma_q(d.c[1], sy[1], df_mul(d.c[0], sy[0])), df_fma_q(d.c[3], sy[3], df_mul(d.c[2], sy[2])));
+    c.E = df_add_q(df_add_q(df_fma_q(d.w[1], s0[1], df_mul(d.w[0], s0[0])),
+                            df_fma_q(d.w[3], s0[3], df_mul(d.w[2], s0[2]))),
+                   R.EF);
+}
+
+// Primitives and raw-moment factors from rho, j and E (the steps of primitives() and
+// the shared part of equilibrium<true>()).  With j_x u_x and j_y u_y formed once,
+// rho u^2 and m5 - m7 are their sum and difference, and u^2 = rho u^2 / rho,
+// u_x^2 - u_y^2 = (m5 - m7) / rho.  Only rho, the operand of the reciprocal, is
+// renormalised (in df_sums).
+template <typename DM, typename L>
+__device__ __forceinline__ void df_chain(const DM &d, DFScalars<L> &c, unsigned *flag)
+{
     c.r = df_rcp(c.rho);
     c.ux = df_mul(c.jx, c.r);
     c.uy = df_mul(c.jy, c.r);
@@ -258,6 +261,15 @@ __device__ __forceinline__ DFScalars<L> df_scalars(const DFModelT<L> &d, const D
     c.m1416 = df_fma_q(c.T, df_fma_q(d.Kp6, c.ru2, df_mul(d.twoKp2, c.P)), df_mul(c.ru2, c.u2));
     c.W4 = df_fma_q(d.Kp4, c.T, c.u2);
     c.m6 = df_mul(c.jx, c.uy);
+}
+
+template <typename L>
+__device__ __forceinline__ DFScalars<L> df_scalars(const DFModelT<L> &d, const DFShiftT<L> &R, const dfl<L> s0[4],
+                                                   const dfl<L> sx[4], const dfl<L> sy[4], unsigned *flag)
+{
+    DFScalars<L> c;
+    df_sums(d, R, s0, sx, sy, c);
+    df_chain(d, c, flag);
     return c;
 }
 
@@ -308,13 +320,10 @@ __device__ __forceinline__ DFScalars<L> df_scalars_sym(const DFModelT<L> &d, con
 {
     DFScalars<L> c;
     c.rho = df_norm(df_add_q(df_add_q(df_add_q(s0[0], s0[1]), df_add_q(s0[2], s0[3])), R.rhoF));
-    c.jx = df_mul(d.c[0], sx[0]);
-    c.E = df_add_q(df_mul(d.w[0], s0[0]), R.EF);
-#pragma unroll
-    for (int g = 1; g < 4; ++g) {
-        c.jx = df_fma_q(d.c[g], sx[g], c.jx);
-        c.E = df_fma_q(d.w[g], s0[g], c.E);
-    }
+    c.jx = df_add_q(df_fma_q(d.c[1], sx[1], df_mul(d.c[0], sx[0])), df_fma_q(d.c[3], sx[3], df_mul(d.c[2], sx[2])));
+    c.E = df_add_q(df_add_q(df_fma_q(d.w[1], s0[1], df_mul(d.w[0], s0[0])),
+                            df_fma_q(d.w[3], s0[3], df_mul(d.w[2], s0[2]))),
+                   R.EF);
     c.r = df_rcp(c.rho);
     c.ux = df_mul(c.jx, c.r);
     c.ru2 = df_mul(c.jx, c.ux);
