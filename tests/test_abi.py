@@ -86,3 +86,50 @@ def test_null_arguments(lib):
     assert lib_.cdbm_step(None, 1) == cdbm.CDBM_EINVAL
     assert lib_.cdbm_sync(None) == cdbm.CDBM_EINVAL
     lib_.cdbm_destroy(None)
+
+
+def test_diagnostic_and_batch_switch_argument_checks(lib):
+    """Argument checks that return before any CUDA call."""
+    lib_ = cdbm.load()
+    assert lib_.cdbm_diag_rcp64(None, None, -1, None) == cdbm.CDBM_EINVAL
+    assert "n < 0" in lib_.cdbm_last_error(None).decode()
+    assert lib_.cdbm_diag_rcp64(None, None, 0, None) == cdbm.CDBM_OK          # nothing to do
+    assert lib_.cdbm_diag_rcp64(None, None, 5, None) == cdbm.CDBM_EINVAL       # NULL with n > 0
+    flops = ctypes.c_double()
+    for blocks, threads, iters in ((0, 128, 1), (1, 100, 1), (1, 2048, 1), (1, 128, 0)):
+        st = lib_.cdbm_diag_fp64_fma(ctypes.c_void_p(16), blocks, threads, iters, None, ctypes.byref(flops))
+        assert st == cdbm.CDBM_EINVAL, (blocks, threads, iters)
+    assert lib_.cdbm_diag_fp64_fma(None, 1, 128, 1, None, ctypes.byref(flops)) == cdbm.CDBM_EINVAL
+    assert lib_.cdbm_batch_set_symmetric(None, 1) == cdbm.CDBM_EINVAL
+
+
+def test_symmetric_velocity_maps(tmp_path):
+    """The index maps of the y-symmetric kernels (cdbm_device.cuh, compiled here as
+    host code) against the geometry of Eq. (2) as the oracle builds it: each
+    velocity's direction signs, the image it holds on a y-symmetric state (same x
+    component, opposite y component), the mirror plane a computed velocity also
+    writes, and the 10 distinct velocities (v_y >= 0, the images of the others)."""
+    import shutil
+    import subprocess
+    import oracle
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("no nvcc")
+    exe = str(tmp_path / "velocity_maps")
+    subprocess.run([nvcc, "-std=c++17", "-I", os.path.join(ROOT, "include"),
+                    "-I", os.path.join(ROOT, "paper_2502_16818_gb300", "csrc"),
+                    os.path.join(ROOT, "tests", "velocity_maps.cu"), "-o", exe], check=True, capture_output=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    rows = [list(map(int, line.split())) for line in out[:16]]
+    distinct = list(map(int, out[16].split()))
+    vx, vy, _ = oracle.velocity_set((1.0, 1.0, 2.0, 2.0), (0.0, 0.0, 0.0, 1.0))
+    image = {i: [k for k in range(16) if vx[k] == vx[i] and vy[k] == -vy[i]][0] for i in range(16)}
+    for i, dx, dy, mirror, partner in rows:
+        assert (dx, dy) == (int(round(vx[i] / abs(vx[i]))) if vx[i] else 0,
+                            int(round(vy[i] / abs(vy[i]))) if vy[i] else 0), i
+        if vy[i] < 0:
+            assert mirror == image[i] and partner == -1, i      # held by its image
+        else:
+            assert mirror == i, i                               # computed
+            assert partner == (image[i] if image[i] != i else -1), i
+    assert distinct == [i for i in range(16) if vy[i] >= 0]
