@@ -67,15 +67,8 @@ __device__ __forceinline__ TS pick(double d, float f)
     if constexpr (kSingle<TS>) return f; else return d;
 }
 
-// One Runge-Kutta stage (kStage 0 or 1) over the nx cells of one tube by the calling
-// block.  g, base and out point at the tube's first cell; planes are P apart.  The
-// arithmetic per cell is the flat (Ny = 1) stage of the single-grid kernels, with the
-// equilibrium in double or, with kDF, in df64.  Plain loads: the buffers are written
-// inside this kernel, so the read-only path may not be used.
-// With kSym the tube's state is y-symmetric (conserved_sym): only the 10 distinct
-// velocities are loaded and computed, each result is stored to its plane and to the
-// plane of its mirror image, and the equilibrium drops the terms of j_y = 0.  The
-// values are those of the general form.
+// The 16 values of cell x of a tube; with kSym only the 10 distinct velocities of a
+// y-symmetric state are loaded and the mirror images copied from them.
 template <typename TS, bool kSym>
 __device__ __forceinline__ void load_state(const TS *g, long long P, int x, TS fs[kNV])
 {
@@ -89,6 +82,15 @@ __device__ __forceinline__ void load_state(const TS *g, long long P, int x, TS f
     }
 }
 
+// One Runge-Kutta stage (kStage 0 or 1) over the nx cells of one tube by the calling
+// block.  g, base and out point at the tube's first cell; planes are P apart.  The
+// arithmetic per cell is the flat (Ny = 1) stage of the single-grid kernels, with the
+// equilibrium in double or, with kDF, in df64.  Plain loads: the buffers are written
+// inside this kernel, so the read-only path may not be used.
+// With kSym the tube's state is y-symmetric (conserved_sym): only the 10 distinct
+// velocities are loaded and computed, each result is stored to its plane and to the
+// plane of its mirror image, and the equilibrium drops the terms of j_y = 0.  The
+// values are those of the general form.
 template <typename TS, int kStage, bool kDF, bool kSym = false>
 __device__ __forceinline__ void tube_stage(const TS *g, const TS *base, TS *out, long long P,
                                            const TubeInfo &t, const ClassConsts &C, TS a_self, TS a_base,
