@@ -298,14 +298,16 @@ __device__ __forceinline__ void tube_stage2(const float *g, const float *base, f
     }
 }
 
-// Register budget: 384 resident threads per SM for the double-precision equilibrium
-// (168 registers at 128 threads) and for the two-column df64 one, whose two cells
-// of float arithmetic take about as many.  The symmetric df64 form keeps less live
-// state and fits 640 threads per SM (102 registers at 128 threads) without spills:
-// 1.15e10 against 1.07e10 cell-updates/s on the 1024-tube ensemble.
+// Register budget (resident threads per SM the registers must allow): 384 for the
+// double-precision equilibrium (168 registers at 128 threads) and for the two-column
+// df64 one, whose two cells of float arithmetic take about as many.  The symmetric
+// forms keep less live state: 512 for FP64 and FP32_BULK (126 / 116 registers at
+// 128 threads, no spills; 1.97e9 / 3.05e9 against 1.95e9 / 2.90e9 cell-updates/s on
+// the 1024-tube ensemble) and 640 for df64 (96 registers; 1.13e10 against 1.07e10).
+constexpr int batch_thread_budget(bool df, bool sym) { return sym ? (df ? 640 : 512) : 384; }
 constexpr int batch_min_blocks(int threads, bool df, bool sym)
 {
-    return (df && sym ? 640 : 384) / threads > 0 ? (df && sym ? 640 : 384) / threads : 1;
+    return batch_thread_budget(df, sym) / threads > 0 ? batch_thread_budget(df, sym) / threads : 1;
 }
 
 template <typename TS, int kThreads, bool kDF, bool kSym>
