@@ -178,10 +178,15 @@ def random_blocks(nx: int, ny: int, seed: int = 0, vset=VSET_SOUND, I: float = 1
     bx = max(1, nx // 7)
     by = max(1, ny // 5)
     shape = ((ny + by - 1) // by, (nx + bx - 1) // bx)
-    rho = np.kron(rng.uniform(0.5, 1.5, shape), np.ones((by, bx)))[:ny, :nx]
-    ux = np.kron(rng.uniform(-0.2, 0.2, shape), np.ones((by, bx)))[:ny, :nx]
-    uy = np.kron(rng.uniform(-0.2, 0.2, shape), np.ones((by, bx)))[:ny, :nx]
-    T = np.kron(rng.uniform(0.7, 1.3, shape), np.ones((by, bx)))[:ny, :nx]
+    iy, ix = np.arange(ny)[:, None] // by, np.arange(nx)[None, :] // bx
+
+    def blocks(lo, hi):              # each drawn value fills a by x bx block
+        return rng.uniform(lo, hi, shape)[iy, ix]
+
+    rho = blocks(0.5, 1.5)
+    ux = blocks(-0.2, 0.2)
+    uy = blocks(-0.2, 0.2)
+    T = blocks(0.7, 1.3)
     dx = 1.0 / nx
     return Workload(name="random_blocks", nx=nx, ny=ny, dx=dx, dy=1.0 / ny, dt=dt, tau=tau,
                     I=float(I), vg=vset[0], eg=vset[1], bc_x=bc[0], bc_y=bc[1], steps=steps,

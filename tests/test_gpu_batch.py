@@ -109,6 +109,32 @@ def test_batch_symmetric_kernels_equal_general_kernels(precision):
         assert np.array_equal(a, c)
 
 
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_batch_tiny_tubes(precision):
+    """Tubes of 1, 2, 3 and 5 cells, where every zero-gradient neighbour index is
+    clamped and the two-cell df64 form has an odd last cell: the symmetric kernels
+    equal the general ones bit for bit, and FP64 matches the oracle."""
+    from paper_2502_16818_gb300 import BatchSolver
+    tubes = [W.ensemble_tube({"nx": n, "rho": (1.0, 0.5), "T": (1.0, 0.8), "I": float(n % 3)}, steps=40)
+             for n in (1, 2, 3, 5, 4, 7)]
+    outs = []
+    for sym in (True, False):
+        b = BatchSolver(tubes, precision=precision)
+        b.init(tubes)
+        b.set_symmetric(sym)
+        b.step(40)
+        b.sync()
+        outs.append(b.macros())
+        b.close()
+    for a, c in zip(*outs):
+        assert np.array_equal(a, c)
+    if precision == 0:
+        for t, w in enumerate(tubes):
+            got = b.tube(outs[0], t)
+            ref = oracle_tube(w, 40)
+            assert rel(got[0], ref[0][0]) <= 1e-10 and rel(got[3], ref[3][0]) <= 1e-10, t
+
+
 def test_batch_with_transverse_velocity_uses_general_kernels():
     """A tube with u_y != 0 is not symmetric: the batch runs the general kernels,
     and each tube still matches the oracle."""
