@@ -56,8 +56,8 @@ BYTES_PER_CELL_STEP_ADJ_BWD = 640 + 384 + 512
 # the stage kernels; valid only while the code of the kernel sources (comments
 # stripped) hashes to TRAFFIC_SHA.
 # Captured at 1024^2 (134 MB per plane set, above L2) and scaled by 16 cells-fold.
-TRAFFIC_SHA = "7a6c2e9cf55ab804"
-TRAFFIC_BYTES_PER_LAUNCH = 5.107e9
+TRAFFIC_SHA = "9c5a2171def617af"
+TRAFFIC_BYTES_PER_LAUNCH = 5.130e9
 
 
 STAGE_SOURCES = ("cdbm_device.cuh", "cdbm_kernels.cu", "cdbm_internal.h")
@@ -89,6 +89,7 @@ def parse():
     p.add_argument("--impl", choices=["cdbm", "reference"], default="cdbm")
     p.add_argument("--n", type=int, default=4096, help="grid size (n x n)")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-aux", action="store_true", help="skip timing the on-demand kernels (init, macros, Delta*, sums)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-variants", action="store_true", help="skip the FP32-bulk and ensemble runs")
     p.add_argument("--ens-steps", type=int, default=200, help="timed steps of the tube ensemble")
@@ -372,6 +373,8 @@ def run_cdbm(a, rank, world, local_rank):
         "decay_rate": decay,
     }
 
+    if not a.no_aux:
+        out["aux_kernels"] = aux_kernels(s, w, stream, torch, cdbm, 8, True)
     if not a.no_e2e:
         out["e2e"] = e2e(a, w, stream, cdbm, s, torch)
     s.close()
@@ -428,6 +431,8 @@ def fp32_variant(a, w, torch, Solver, precision, ref64, value64, amp0, note):
     ms = e0.elapsed_time(e1)
     s.sync()
     rho, ux, uy, T = s.macros()
+    from paper_2502_16818_gb300 import cdbm
+    aux = None if a.no_aux else aux_kernels(s, w, stream, torch, cdbm, 4, False)
     s.close()
     l2 = float(torch.linalg.norm(rho - rho64) / torch.linalg.norm(rho64))
     errs = field_errors((rho, ux, uy, T), ref64, W.gamma_of(w.I), torch)
@@ -438,7 +443,7 @@ def fp32_variant(a, w, torch, Solver, precision, ref64, value64, amp0, note):
             "decay_rate_measured": float(-np.log(amp1 / amp0) / (a.steps * w.dt)),
             "hbm_gbs": BYTES_PER_CELL_STEP_FP32 * w.nx * w.ny * a.steps / (ms * 1e-3) / 1e9,
             "hbm_frac_of_measured": BYTES_PER_CELL_STEP_FP32 * w.nx * w.ny * a.steps / (ms * 1e-3) / 1e9
-                                    / measured_hbm(), "note": note}
+                                    / measured_hbm(), "aux_kernels": aux, "note": note}
 
 
 def full_length_vortex(a, w, torch, Solver):
@@ -633,6 +638,47 @@ def adjoint(a, torch):
             "forward_hbm_gbs": fwd_gbs, "forward_hbm_frac_of_measured": fwd_gbs / measured_hbm(),
             "backward_hbm_gbs": bwd_gbs, "backward_hbm_frac_of_measured": bwd_gbs / measured_hbm(),
             "bytes_per_cell_step": {"forward": BYTES_PER_CELL_STEP, "backward": BYTES_PER_CELL_STEP_ADJ_BWD}}
+
+
+def aux_kernels(s, w, stream, torch, cdbm, state_bytes, with_init, reps=10):
+    """The on-demand kernels on the resident vortex state, each call timed with CUDA
+    events on the solver's stream (mean of `reps` after one untimed call), with the
+    HBM GB/s of its algorithmic bytes per cell: init from device fields (reads rho,
+    u, T: 32 B; writes the 16 planes), macros (reads the planes, writes rho, u, T:
+    32 B), Delta* (reads the planes, writes 12 doubles: 96 B; it rebuilds the
+    central moments of every cell from its raw moments) and the conserved sums
+    (reads the planes; a synchronous call that returns 4
+    doubles).  Delta*, macros and the sums are bound by the FP64 pipe at these
+    byte counts (167, 51 and 22 FP64 instructions per cell on the FP64 state).  state_bytes:
+    bytes per stored value (8 for FP64, 4 for the single-precision states)."""
+    cells = w.nx * w.ny
+    planes = 16 * state_bytes
+    with torch.cuda.stream(stream):
+        fields = [torch.from_numpy(x).to("cuda") for x in (w.rho, w.ux, w.uy, w.T)]
+        outs = [torch.empty((w.ny, w.nx), dtype=torch.float64, device="cuda") for _ in range(4)]
+        tne = torch.empty((12, w.ny, w.nx), dtype=torch.float64, device="cuda")
+    stream.synchronize()
+    calls = [("macros_kernel", planes + 32, lambda: cdbm.cdbm_macros(s.ctx, *(o.data_ptr() for o in outs))),
+             ("tne_kernel (Delta*)", planes + 96, lambda: cdbm.cdbm_tne(s.ctx, tne.data_ptr())),
+             ("sums_partial_kernel + sums_final_kernel (conserved sums)", planes,
+              lambda: cdbm.cdbm_conserved_sums(s.ctx))]
+    if with_init:
+        calls.insert(0, ("init_kernel", 32 + planes, lambda: cdbm.cdbm_init(s.ctx, *(f.data_ptr() for f in fields))))
+    res = {}
+    for name, per_cell, call in calls:
+        call()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            call()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        gbs = per_cell * cells / (ms * 1e-3) / 1e9
+        res[name.split(" ")[0]] = {"kernel": name, "ms": ms, "bytes_per_cell": per_cell, "hbm_gbs": gbs,
+                                   "hbm_frac_of_measured": gbs / measured_hbm()}
+    return res
 
 
 def e2e(a, w, stream, cdbm, s, torch):

@@ -169,14 +169,17 @@ cdbm_status cdbm_macros(cdbm_ctx *ctx, double *rho, double *ux, double *uy, doub
  * cdbm_tne -- nonequilibrium central moments of the current state, Eqs. (8)-(11):
  * out[k][ny][nx], k = 0..11 = rows 5..16 of Eq. (6) applied to f - f_eq:
  * Delta2 {xx, xy, yy}, Delta31 {x, y}, Delta3 {xxx, xxy, xyy, yyy},
- * Delta42 {xx, xy, yy}.  out: host or device.
+ * Delta42 {xx, xy, yy}.  Computed as the central moments of f about u minus the
+ * prescribed central moments of Eq. (7) (equal to M(u) f_eq by the definition of
+ * f_eq).  out: host or device (a host copy synchronises the stream).
  */
 cdbm_status cdbm_tne(cdbm_ctx *ctx, double *out);
 
 /*
  * cdbm_conserved_sums -- domain totals of rho, rho u_x, rho u_y and
- * sum_i f_i (v_i^2 + eta_i^2) (twice the total energy) into out[4] (host).
- * Deterministic (fixed reduction order).  Synchronous.
+ * sum_i f_i (v_i^2 + eta_i^2) (twice the total energy) into out[4] (host):
+ * each velocity plane is summed over the cells in double precision, then the 16
+ * plane totals are weighted.  Deterministic (fixed reduction order).  Synchronous.
  */
 cdbm_status cdbm_conserved_sums(cdbm_ctx *ctx, double out[4]);
 

@@ -55,7 +55,7 @@ struct cdbm_ctx {
     void *f;                      // state [16][ny][nx] in storage precision
     void *f1;                     // stage buffer [16][ny][nx] in storage precision; also
                                   // double staging (16 planes) for host I/O and conversions
-    double *partials;             // conserved-sum partials [nblocks][4]
+    double *partials;             // conserved-sum partials [nblocks][16] (plane sums), field means [nblocks][4]
     double *sums;                 // 4 doubles
     unsigned *flag;               // device error flags
     unsigned *flag_host;          // pinned mirror
@@ -506,7 +506,7 @@ cdbm_status cdbm_create(const cdbm_grid *grid, const cdbm_vset *vset, double I, 
     const size_t f1bytes = sizeof(double) * kNV * c->plane;
     c->f = ctx_alloc(c, fbytes);
     c->f1 = ctx_alloc(c, f1bytes);
-    c->partials = (double *)ctx_alloc(c, sizeof(double) * 4 * c->sum_blocks + sizeof(double) * 4 + 256);
+    c->partials = (double *)ctx_alloc(c, sizeof(double) * kNV * c->sum_blocks + sizeof(double) * 4 + 256);
     if (!c->f || !c->f1 || !c->partials || cudaMallocHost(&c->flag_host, sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();
         ctx_free(c, c->f, fbytes);
@@ -516,7 +516,7 @@ cdbm_status cdbm_create(const cdbm_grid *grid, const cdbm_vset *vset, double I, 
         delete c;
         return create_err(CDBM_ENOMEM, "device allocation of %zu bytes failed", fbytes + f1bytes);
     }
-    c->sums = c->partials + 4 * c->sum_blocks;
+    c->sums = c->partials + kNV * c->sum_blocks;
     c->flag = (unsigned *)(c->sums + 4);
     *c->flag_host = 0;
     if (cudaMemsetAsync(c->flag, 0, sizeof(unsigned), c->stream) != cudaSuccess) {
@@ -969,7 +969,7 @@ void cdbm_destroy(cdbm_ctx *c)
     c->ckpt.clear();
     ctx_free(c, c->f, storage_bytes(c->precision) * kNV * c->plane);
     ctx_free(c, c->f1, sizeof(double) * kNV * c->plane);
-    ctx_free(c, c->partials, sizeof(double) * 4 * c->sum_blocks + sizeof(double) * 4 + 256);
+    ctx_free(c, c->partials, sizeof(double) * kNV * c->sum_blocks + sizeof(double) * 4 + 256);
     cudaStreamSynchronize(c->stream);
     if (c->flag_host) cudaFreeHost(c->flag_host);
     cudaGetLastError();

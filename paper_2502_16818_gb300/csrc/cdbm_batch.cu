@@ -394,17 +394,24 @@ __global__ void __launch_bounds__(128) batch_macros_kernel(const BatchArgs a, co
          c += (long long)gridDim.x * blockDim.x) {
         const TubeInfo &t = tubes[tube_of(offs, ntubes, c)];
         const ModelConsts &m = a.cls[t.cls].m;
+        // the operations of the single-grid macros kernel: moments of the stored
+        // values (plus the reference equilibrium's for a single-precision state)
+        // and one reciprocal of rho
         double fc[kNV];
 #pragma unroll
-        for (int i = 0; i < kNV; ++i)
-            fc[i] = kSingle<TS> ? t.Fg[i >> 2] + (double)f[i * a.P + c] : (double)f[i * a.P + c];
-        const Cons q = conserved(fc, m);
-        const double u = q.jx / q.rho, v = q.jy / q.rho;
+        for (int i = 0; i < kNV; ++i) fc[i] = widen(f[i * a.P + c]);
+        Cons q = conserved(fc, m);
+        if constexpr (kSingle<TS>) {
+            q.rho += t.rhoF;
+            q.E += t.EF;
+        }
+        const double r = rcp64(q.rho);
+        const double u = q.jx * r, v = q.jy * r;
         const double ru2 = fma(q.jx, u, q.jy * v);
         if (rho) rho[c] = q.rho;
         if (ux) ux[c] = u;
         if (uy) uy[c] = v;
-        if (T) T[c] = (q.E - ru2) / (m.K * q.rho);
+        if (T) T[c] = (q.E - ru2) * m.invK * r;
     }
 }
 

@@ -30,10 +30,6 @@ constexpr int kStageThreads = 128;
 #endif
 constexpr int stage_min_blocks(bool df) { return df ? CDBM_STAGE_MIN_BLOCKS_DF : CDBM_STAGE_MIN_BLOCKS; }
 
-// Stored value of velocity i -> f_i in double (adds the reference F to an FP32 deviation).
-__device__ __forceinline__ double widen(const FieldArgs &, double v, int) { return v; }
-__device__ __forceinline__ double widen(const FieldArgs &a, float v, int i) { return a.Fg[i >> 2] + (double)v; }
-
 // ---------------------------------------------------------------- init (K0)
 
 template <typename TS>
@@ -486,8 +482,38 @@ __global__ void __launch_bounds__(kStageThreads, kMarch2MinBlocks)
 
 // ------------------------------------------------------------ macros (K3)
 
+// Moments of the reference equilibrium F that a single-precision state stores its
+// deviation g = f - F from: F_g on the four members of group g, so F carries no
+// momentum and no odd moment.  The moments are linear in f, so the kernels take the
+// moments of g (each value widened exactly) and add these; zero for FP64.
+struct RefMoments {
+    double rho, E;     // sum F, sum F (v^2 + eta^2)
+    double Rxx, Rwxx;  // sum F v_x^2 (= sum F v_y^2), sum F (v^2 + eta^2) v_x^2 (= ... v_y^2)
+};
+
+RefMoments ref_moments(const FieldArgs &a, bool single)
+{
+    RefMoments r{0.0, 0.0, 0.0, 0.0};
+    if (!single) return r;
+    for (int g = 0; g < 4; ++g) {
+        const double s0 = 4.0 * a.Fg[g];
+        const double ex = (g & 1) == 0 ? 2.0 * a.Fg[g] : s0;    // members with v_x != 0
+        const double c2 = a.m.c[g] * a.m.c[g];
+        r.rho += s0;
+        r.E += a.m.w[g] * s0;
+        r.Rxx += c2 * ex;
+        r.Rwxx += a.m.w[g] * c2 * ex;
+    }
+    return r;
+}
+
+// The value stored for velocity i as a double: f itself, or the deviation g (the
+// reference moments are added afterwards).
+__device__ __forceinline__ double stored(double v) { return v; }
+__device__ __forceinline__ double stored(float v) { return widen_f32(v); }
+
 template <typename TS>
-__global__ void __launch_bounds__(128) macros_kernel(const FieldArgs a, const TS *__restrict__ f,
+__global__ void __launch_bounds__(128) macros_kernel(const FieldArgs a, const RefMoments F, const TS *__restrict__ f,
                                                       double *rho, double *ux, double *uy, double *T)
 {
     const size_t P = (size_t)a.nx * a.ny;
@@ -495,63 +521,122 @@ __global__ void __launch_bounds__(128) macros_kernel(const FieldArgs a, const TS
          c += (size_t)gridDim.x * blockDim.x) {
         double fc[kNV];
 #pragma unroll
-        for (int i = 0; i < kNV; ++i) fc[i] = widen(a, f[i * P + c], i);
-        const Cons q = conserved(fc, a.m);
-        const double u = q.jx / q.rho, v = q.jy / q.rho;
+        for (int i = 0; i < kNV; ++i) fc[i] = stored(f[i * P + c]);
+        Cons q = conserved(fc, a.m);
+        if constexpr (kSingle<TS>) {
+            q.rho += F.rho;
+            q.E += F.E;
+        }
+        const double r = rcp64(q.rho);
+        const double u = q.jx * r, v = q.jy * r;
         const double ru2 = fma(q.jx, u, q.jy * v);
         if (rho) rho[c] = q.rho;
         if (ux) ux[c] = u;
         if (uy) uy[c] = v;
-        if (T) T[c] = (q.E - ru2) / (a.m.K * q.rho);
+        if (T) T[c] = (q.E - ru2) * a.m.invK * r;
     }
 }
 
 // ------------------------------------------------------------ TNE (K4)
 
-// Rows 5..16 of M(u) (Eq. 6) applied to f - f_eq: Delta* of Eqs. (8)-(11).
+// Powers of the group speed component c_g (v = (+-c_g, 0), (0, +-c_g) on the axis
+// groups, (+-c_g, +-c_g) on the diagonal ones) and of W_g = |v|^2 + eta_g^2.
+struct TneConsts {
+    double c[4], c2[4], c3[4], W[4], Wc[4], Wc2[4];
+};
+
+// Rows 5..16 of M(u) (Eq. 6) applied to f - f_eq: Delta* of Eqs. (8)-(11).  f_eq is
+// defined by M(u) f_eq = fbar, the prescribed central moments of Eq. (7), so Delta*
+// is the central moments of f about u minus rows 5..16 of fbar, whose only nonzero
+// entries are rho T (xx, yy of the second order) and (K + 2) rho T^2 (xx, yy of the
+// fourth).  The central moments follow from the raw moments R_k = sum_i f_i row_k(v_i)
+// by the binomial expansion of (v - u) with j = rho u; the raw moments of a group
+// come from its members' sum, x and y differences, the x and y pair sums (axis
+// groups) and the xy parity (diagonal groups).
 template <typename TS>
-__global__ void __launch_bounds__(128) tne_kernel(const FieldArgs a, const TS *__restrict__ f,
-                                                   double *__restrict__ out)
+__global__ void __launch_bounds__(128) tne_kernel(const FieldArgs a, const TneConsts t, const RefMoments F,
+                                                   const TS *__restrict__ f, double *__restrict__ out)
 {
     const size_t P = (size_t)a.nx * a.ny;
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < P;
          c += (size_t)gridDim.x * blockDim.x) {
         double fc[kNV];
 #pragma unroll
-        for (int i = 0; i < kNV; ++i) fc[i] = widen(a, f[i * P + c], i);
-        const Cons q = conserved(fc, a.m);
-        const double u = q.jx / q.rho, v = q.jy / q.rho;
-        const double jyuy = q.jy * v;
-        const double ru2 = fma(q.jx, u, jyuy);
-        const double p = (q.E - ru2) * a.m.invK;
-        const double T = p / q.rho;
-        double fe[kNV];
-        equilibrium(a.eq, a.m, q.rho, q.E, q.jx, q.jy, u, v, ru2, jyuy, p, T, fe);
-        double acc[12];
+        for (int i = 0; i < kNV; ++i) fc[i] = stored(f[i * P + c]);
+        // group components: s0 sum, sx / sy odd in x / y, ex / ey the x / y pairs
+        // (axis), sxy odd in x and y (diagonal)
+        double s0[4], sx[4], sy[4], ex[2], ey[2], sxy[2];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) acc[k] = 0.0;
-#pragma unroll
-        for (int i = 0; i < kNV; ++i) {
-            const double d = fc[i] - fe[i];
-            const double cx = a.vx[i] - u, cy = a.vy[i] - v;
-            const double cxx = cx * cx, cxy = cx * cy, cyy = cy * cy;
-            const double w = fma(a.eta[i], a.eta[i], cxx + cyy);
-            const double dw = d * w;
-            acc[0] = fma(d, cxx, acc[0]);
-            acc[1] = fma(d, cxy, acc[1]);
-            acc[2] = fma(d, cyy, acc[2]);
-            acc[3] = fma(dw, cx, acc[3]);
-            acc[4] = fma(dw, cy, acc[4]);
-            acc[5] = fma(d * cxx, cx, acc[5]);
-            acc[6] = fma(d * cxx, cy, acc[6]);
-            acc[7] = fma(d * cyy, cx, acc[7]);
-            acc[8] = fma(d * cyy, cy, acc[8]);
-            acc[9] = fma(dw, cxx, acc[9]);
-            acc[10] = fma(dw, cxy, acc[10]);
-            acc[11] = fma(dw, cyy, acc[11]);
+        for (int g = 0; g < 4; ++g) {
+            const double *q = fc + 4 * g;
+            if ((g & 1) == 0) {          // E N W S
+                ex[g >> 1] = q[0] + q[2];
+                ey[g >> 1] = q[1] + q[3];
+                sx[g] = q[0] - q[2];
+                sy[g] = q[1] - q[3];
+                s0[g] = ex[g >> 1] + ey[g >> 1];
+            } else {                     // NE NW SW SE
+                const double e = q[0] + q[3], w = q[1] + q[2];
+                sx[g] = e - w;
+                sy[g] = (q[0] + q[1]) - (q[2] + q[3]);
+                sxy[g >> 1] = (q[0] + q[2]) - (q[1] + q[3]);
+                s0[g] = e + w;
+            }
         }
+        auto dot = [](const double *k, const double *x) {
+            return fma(k[3], x[3], fma(k[2], x[2], fma(k[1], x[1], k[0] * x[0])));
+        };
+        // raw moments R1..R16 (rows of Eq. 6 at u = 0)
+        double rho = (s0[0] + s0[1]) + (s0[2] + s0[3]);
+        const double jx = dot(t.c, sx), jy = dot(t.c, sy);
+        double E = dot(t.W, s0);
+        double Rxx = fma(t.c2[3], s0[3], fma(t.c2[2], ex[1], fma(t.c2[1], s0[1], t.c2[0] * ex[0])));
+        double Ryy = fma(t.c2[3], s0[3], fma(t.c2[2], ey[1], fma(t.c2[1], s0[1], t.c2[0] * ey[0])));
+        const double Rxy = fma(t.c2[3], sxy[1], t.c2[1] * sxy[0]);
+        const double Rwx = dot(t.Wc, sx), Rwy = dot(t.Wc, sy);
+        const double Rxxx = dot(t.c3, sx), Ryyy = dot(t.c3, sy);
+        const double Rxxy = fma(t.c3[3], sy[3], t.c3[1] * sy[1]);
+        const double Rxyy = fma(t.c3[3], sx[3], t.c3[1] * sx[1]);
+        double Rwxx = fma(t.Wc2[3], s0[3], fma(t.Wc2[2], ex[1], fma(t.Wc2[1], s0[1], t.Wc2[0] * ex[0])));
+        double Rwyy = fma(t.Wc2[3], s0[3], fma(t.Wc2[2], ey[1], fma(t.Wc2[1], s0[1], t.Wc2[0] * ey[0])));
+        const double Rwxy = fma(t.Wc2[3], sxy[1], t.Wc2[1] * sxy[0]);
+        if constexpr (kSingle<TS>) {    // the reference equilibrium's even moments
+            rho += F.rho;
+            E += F.E;
+            Rxx += F.Rxx;
+            Ryy += F.Rxx;
+            Rwxx += F.Rwxx;
+            Rwyy += F.Rwxx;
+        }
+        // primitives: u = j / rho, p = rho T = (E - rho u^2) / K
+        const double r = rcp64(rho);
+        const double ux = jx * r, uy = jy * r;
+        const double uxuy = ux * uy, u2 = fma(ux, ux, uy * uy);
+        const double p = (E - fma(jx, ux, jy * uy)) * a.m.invK;
+        const double q4 = a.m.Kp2 * p * (p * r);                 // (K + 2) rho T^2
+        const double ax = fma(uy, Rxy, ux * Rxx);                // sum f (v.u) v_x
+        const double ay = fma(uy, Ryy, ux * Rxy);                // sum f (v.u) v_y
+        // central moments about u, minus fbar
+        const double Cxx = fma(-ux, jx, Rxx), Cxy = fma(-ux, jy, Rxy), Cyy = fma(-uy, jy, Ryy);
+        const double d[12] = {
+            Cxx - p,
+            Cxy,
+            Cyy - p,
+            fma(2.0 * u2, jx, fma(-2.0, ax, fma(-ux, E, Rwx))),
+            fma(2.0 * u2, jy, fma(-2.0, ay, fma(-uy, E, Rwy))),
+            fma(2.0 * jx, ux * ux, fma(-3.0 * ux, Rxx, Rxxx)),
+            fma(2.0 * jx, uxuy, fma(-2.0 * ux, Rxy, fma(-uy, Rxx, Rxxy))),
+            fma(2.0 * jy, uxuy, fma(-2.0 * uy, Rxy, fma(-ux, Ryy, Rxyy))),
+            fma(2.0 * jy, uy * uy, fma(-3.0 * uy, Ryy, Ryyy)),
+            fma(u2, Cxx, fma(-2.0 * jx * ux, u2, fma(4.0 * ux, ax, fma(-2.0, fma(uy, Rxxy, ux * Rxxx),
+                fma(ux * ux, E, fma(-2.0 * ux, Rwx, Rwxx)))))) - q4,
+            fma(u2, Cxy, fma(-2.0, fma(jx * uy, u2, fma(-ux, ay, fma(-uy, ax, fma(uy, Rxyy, ux * Rxxy)))),
+                fma(uxuy, E, fma(-ux, Rwy, fma(-uy, Rwx, Rwxy))))),
+            fma(u2, Cyy, fma(-2.0 * jy * uy, u2, fma(4.0 * uy, ay, fma(-2.0, fma(uy, Ryyy, ux * Rxyy),
+                fma(uy * uy, E, fma(-2.0 * uy, Rwy, Rwyy)))))) - q4,
+        };
 #pragma unroll
-        for (int k = 0; k < 12; ++k) out[k * P + c] = acc[k];
+        for (int k = 0; k < 12; ++k) out[k * P + c] = d[k];
     }
 }
 
@@ -559,46 +644,77 @@ __global__ void __launch_bounds__(128) tne_kernel(const FieldArgs a, const TS *_
 
 constexpr int kSumThreads = 256;
 
-// Block b reduces cells [b*chunk, (b+1)*chunk) in a fixed order and writes its
-// four partial sums; the order depends only on the grid size and nblocks.
+// The conserved totals are sums over the 16 velocity planes, each weighted by a
+// constant of its velocity (1, v_x, v_y, |v|^2 + eta^2), so the cells are reduced
+// plane by plane (one FP64 addition per value) and the weights are applied to the
+// 16 plane totals at the end.  Block b reduces cells [b*chunk, (b+1)*chunk) in a
+// fixed order and writes its 16 plane sums; the order depends only on the grid size
+// and nblocks.  A single-precision state adds its stored deviations g (widened
+// exactly), and the reference equilibrium's share, cells x F_g, is added to the
+// plane totals.
 template <typename TS>
 __global__ void __launch_bounds__(kSumThreads) sums_partial_kernel(const FieldArgs a,
                                                                    const TS *__restrict__ f,
                                                                    double *__restrict__ partials)
 {
-    __shared__ double sh[4][kSumThreads];
+    __shared__ double sh[kNV][kSumThreads / 32];
     const size_t P = (size_t)a.nx * a.ny;
     const size_t chunk = (P + gridDim.x - 1) / gridDim.x;
     const size_t lo = blockIdx.x * chunk;
     const size_t hi = lo + chunk < P ? lo + chunk : P;
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    double s[kNV];
+#pragma unroll
+    for (int i = 0; i < kNV; ++i) s[i] = 0.0;
     for (size_t c = lo + threadIdx.x; c < hi; c += kSumThreads) {
-        double fc[kNV];
+        // A single-precision value is widened by the conversion instruction (at the
+        // FP64 pipe's rate) for half the planes and on the integer pipe for the
+        // other half, which keeps both units about equally busy.
 #pragma unroll
-        for (int i = 0; i < kNV; ++i) fc[i] = widen(a, f[i * P + c], i);
-        const Cons q = conserved(fc, a.m);
-        s[0] += q.rho;
-        s[1] += q.jx;
-        s[2] += q.jy;
-        s[3] += q.E;
+        for (int i = 0; i < kNV; ++i) {
+            const TS v = f[i * P + c];
+            s[i] += i < kNV / 2 ? (double)v : stored(v);
+        }
     }
+    // warp tree (fixed lane order), then the warps' sums in warp order
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] = s[k];
+    for (int i = 0; i < kNV; ++i) {
+        double v = s[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[i][warp] = v;
+    }
     __syncthreads();
-    for (int w = kSumThreads / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w)
-            for (int k = 0; k < 4; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
-        __syncthreads();
+    if (threadIdx.x < kNV) {
+        double v = 0.0;
+#pragma unroll
+        for (int w = 0; w < kSumThreads / 32; ++w) v += sh[threadIdx.x][w];
+        partials[blockIdx.x * kNV + threadIdx.x] = v;
     }
-    if (threadIdx.x < 4) partials[blockIdx.x * 4 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-__global__ void sums_final_kernel(const double *__restrict__ partials, int nblocks, double *out4)
+// Plane totals in block order, then rho, j_x, j_y and E from them (velocity order).
+__global__ void sums_final_kernel(const FieldArgs a, const double *__restrict__ partials, int nblocks,
+                                  bool single, double *out4)
 {
-    if (threadIdx.x < 4) {
-        double s = 0.0;
-        for (int b = 0; b < nblocks; ++b) s += partials[b * 4 + threadIdx.x];
-        out4[threadIdx.x] = s;
+    __shared__ double tot[kNV];
+    if (threadIdx.x < kNV) {
+        const int i = threadIdx.x;
+        double v = 0.0;
+        for (int b = 0; b < nblocks; ++b) v += partials[b * kNV + i];
+        if (single) v = fma((double)a.nx * (double)a.ny, a.Fg[i >> 2], v);
+        tot[i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int i = 0; i < kNV; ++i) {
+            r[0] += tot[i];
+            r[1] = fma(a.vx[i], tot[i], r[1]);
+            r[2] = fma(a.vy[i], tot[i], r[2]);
+            r[3] = fma(fma(a.vx[i], a.vx[i], fma(a.vy[i], a.vy[i], a.eta[i] * a.eta[i])), tot[i], r[3]);
+        }
+        for (int k = 0; k < 4; ++k) out4[k] = r[k];
     }
 }
 
@@ -648,6 +764,15 @@ __global__ void __launch_bounds__(kSumThreads) means_partial_kernel(const double
     if (threadIdx.x < 2) partials[blockIdx.x * 4 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
+__global__ void means_final_kernel(const double *__restrict__ partials, int nblocks, double *out2)
+{
+    if (threadIdx.x < 2) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks; ++b) s += partials[b * 4 + threadIdx.x];
+        out2[threadIdx.x] = s;
+    }
+}
+
 unsigned grid_for(size_t cells, int threads)
 {
     size_t b = (cells + threads - 1) / threads;
@@ -689,20 +814,31 @@ cudaError_t launch_macros(const FieldArgs &a, const void *f, int prec, double *r
                           double *uy, double *T, cudaStream_t s)
 {
     const unsigned nb = grid_for((size_t)a.nx * a.ny, 128);
+    const RefMoments F = ref_moments(a, single_storage(prec));
     if (single_storage(prec))
-        macros_kernel<float><<<nb, 128, 0, s>>>(a, (const float *)f, rho, ux, uy, T);
+        macros_kernel<float><<<nb, 128, 0, s>>>(a, F, (const float *)f, rho, ux, uy, T);
     else
-        macros_kernel<double><<<nb, 128, 0, s>>>(a, (const double *)f, rho, ux, uy, T);
+        macros_kernel<double><<<nb, 128, 0, s>>>(a, F, (const double *)f, rho, ux, uy, T);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tne(const FieldArgs &a, const void *f, int prec, double *out, cudaStream_t s)
 {
+    TneConsts t;
+    for (int g = 0; g < 4; ++g) {
+        t.c[g] = a.m.c[g];
+        t.c2[g] = a.m.c[g] * a.m.c[g];
+        t.c3[g] = t.c2[g] * a.m.c[g];
+        t.W[g] = a.m.w[g];
+        t.Wc[g] = a.m.w[g] * a.m.c[g];
+        t.Wc2[g] = a.m.w[g] * t.c2[g];
+    }
     const unsigned nb = grid_for((size_t)a.nx * a.ny, 128);
+    const RefMoments F = ref_moments(a, single_storage(prec));
     if (single_storage(prec))
-        tne_kernel<float><<<nb, 128, 0, s>>>(a, (const float *)f, out);
+        tne_kernel<float><<<nb, 128, 0, s>>>(a, t, F, (const float *)f, out);
     else
-        tne_kernel<double><<<nb, 128, 0, s>>>(a, (const double *)f, out);
+        tne_kernel<double><<<nb, 128, 0, s>>>(a, t, F, (const double *)f, out);
     return cudaGetLastError();
 }
 
@@ -713,7 +849,7 @@ cudaError_t launch_sums(const FieldArgs &a, const void *f, int prec, double *par
         sums_partial_kernel<float><<<nblocks, kSumThreads, 0, s>>>(a, (const float *)f, partials);
     else
         sums_partial_kernel<double><<<nblocks, kSumThreads, 0, s>>>(a, (const double *)f, partials);
-    sums_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, out4);
+    sums_final_kernel<<<1, 32, 0, s>>>(a, partials, nblocks, single_storage(prec), out4);
     return cudaGetLastError();
 }
 
@@ -736,7 +872,7 @@ cudaError_t launch_field_means(const double *rho, const double *T, size_t n, dou
                                int nblocks, double *out2, cudaStream_t s)
 {
     means_partial_kernel<<<nblocks, kSumThreads, 0, s>>>(rho, T, n, partials);
-    sums_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, out2);
+    means_final_kernel<<<1, 32, 0, s>>>(partials, nblocks, out2);
     return cudaGetLastError();
 }
 

@@ -52,3 +52,13 @@ def test_bench_line_has_the_contract_keys():
     assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] > 0
     for mode in ("fp32_bulk", "fp32_df64"):
         assert d[mode]["l2_density_error_vs_fp64"] <= 1e-5
+    # the on-demand kernels, each with its time and HBM GB/s
+    names = {"fp64": ("init_kernel", "macros_kernel", "tne_kernel", "sums_partial_kernel")}
+    names["fp32_bulk"] = names["fp32_df64"] = names["fp64"][1:]
+    for mode, keys in names.items():
+        aux = d["aux_kernels"] if mode == "fp64" else d[mode]["aux_kernels"]
+        assert sorted(aux) == sorted(keys), (mode, sorted(aux))
+        for k in keys:
+            row = aux[k]
+            assert row["ms"] > 0 and row["hbm_gbs"] > 0
+            assert abs(row["hbm_gbs"] - row["bytes_per_cell"] * cells / (row["ms"] * 1e-3) / 1e9) <= 1e-9 * row["hbm_gbs"]
