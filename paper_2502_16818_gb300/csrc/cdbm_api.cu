@@ -581,6 +581,12 @@ cdbm_status cdbm_init(cdbm_ctx *c, const double *rho, const double *ux, const do
                    "init launch"))
         return c->err;
     if (any_host && cuda_check(c, cudaStreamSynchronize(c->stream), "cdbm_init sync")) return c->err;
+    // the step graph of the stage-launch path, built and uploaded here so that the
+    // first long cdbm_step does not pay for it
+    if (!c->graph && !(c->small.ok && c->small_enabled)) {
+        if (build_graph(c)) return c->err;
+        if (cuda_check(c, cudaGraphUpload(c->graph, c->stream), "graph upload")) return c->err;
+    }
     c->t = 0.0;
     c->state_set = true;
     c->step_count = 0;
