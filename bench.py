@@ -101,7 +101,7 @@ def parse():
     p.add_argument("--adj-every", type=int, default=200, help="checkpoint interval of the adjoint run")
     p.add_argument("--adj-n", type=int, default=1024, help="grid size of the adjoint run")
     p.add_argument("--full-steps", type=int, default=2000,
-                   help="steps of the full-length vortex runs in all three precisions (0: skip them)")
+                   help="steps of the full-length vortex runs in all four precisions (0: skip them)")
     return p.parse_args()
 
 
@@ -303,7 +303,8 @@ def run_cdbm(a, rank, world, local_rank):
     import torch
     import torch.distributed as dist
 
-    from paper_2502_16818_gb300 import CDBM_FP32_BULK, CDBM_FP32_DF64, CDBM_FP64, Solver, cdbm, replicas
+    from paper_2502_16818_gb300 import (CDBM_FP32_BULK, CDBM_FP32_DEV, CDBM_FP32_DF64, CDBM_FP64, Solver, cdbm,
+                                        replicas)
 
     torch.cuda.set_device(local_rank)
     w = workload(a.n)
@@ -388,6 +389,10 @@ def run_cdbm(a, rank, world, local_rank):
         out["fp32_df64"] = fp32_variant(a, w, torch, Solver, CDBM_FP32_DF64, (rho64, ux64, uy64, T64), value, amp0,
                                         "as fp32_bulk, with sums, moment shift and equilibrium product in "
                                         "double-float arithmetic on the FP32 pipe")
+        out["fp32_dev"] = fp32_variant(a, w, torch, Solver, CDBM_FP32_DEV, (rho64, ux64, uy64, T64), value, amp0,
+                                       "all in single precision: the state as its deviation from the reference "
+                                       "equilibrium and the equilibrium formed from the deviations of the moments "
+                                       "(not the FP64 moment shift and product of fp32_bulk)")
         if a.full_steps > 0:
             out["config3_full"] = full_length_vortex(a, w, torch, Solver)
         if not a.no_ensemble:
@@ -450,13 +455,13 @@ def fp32_variant(a, w, torch, Solver, precision, ref64, value64, amp0, note):
 
 def full_length_vortex(a, w, torch, Solver):
     """The vortex run for its configured length (2000 steps, t = 0.01) in FP64,
-    FP32_BULK and FP32_DF64, whatever --steps is: each run timed as a whole, the
+    FP32_BULK, FP32_DF64 and FP32_DEV, whatever --steps is: each run timed as a whole, the
     Taylor-Green amplitude sampled every 100 steps, the decay rate fitted (least
     squares on log amplitude) over the last 1000 steps against the Navier-Stokes
     rate 2 nu k^2 with nu = T tau (Eqs. 22-23), and the per-field errors of the
     single-precision runs against the FP64 run at the last step."""
     import numpy as np
-    from paper_2502_16818_gb300 import CDBM_FP32_BULK, CDBM_FP32_DF64, CDBM_FP64, workloads as W
+    from paper_2502_16818_gb300 import CDBM_FP32_BULK, CDBM_FP32_DEV, CDBM_FP32_DF64, CDBM_FP64, workloads as W
     steps = a.full_steps
     every = 100 if steps % 100 == 0 else steps
     k = w.extra["k"]
@@ -464,7 +469,8 @@ def full_length_vortex(a, w, torch, Solver):
     mode = torch.cos(k * x)[:, None] * torch.sin(k * x)[None, :]
     res = {"steps": steps, "t_end": steps * w.dt, "sample_every": every}
     finals = {}
-    for label, prec in (("fp64", CDBM_FP64), ("fp32_bulk", CDBM_FP32_BULK), ("fp32_df64", CDBM_FP32_DF64)):
+    for label, prec in (("fp64", CDBM_FP64), ("fp32_bulk", CDBM_FP32_BULK), ("fp32_df64", CDBM_FP32_DF64),
+                        ("fp32_dev", CDBM_FP32_DEV)):
         st = torch.cuda.Stream()
         with torch.cuda.stream(st):
             s = Solver.from_workload(w, stream=st, precision=prec)
@@ -562,14 +568,15 @@ def configs(a, torch):
     """Wall time of the paper-scale configurations on the GPU (CUDA events around the
     whole run, state resident): Sod (500 cells, 10^4 steps), Lax (2000 cells, 10^4
     steps) and the 512^2 sound wave for I = 0, 1, 3 (2000 steps), in FP64 and with
-    the single-precision state and df64 equilibrium."""
-    from paper_2502_16818_gb300 import CDBM_FP32_DF64, CDBM_FP64, Solver, workloads as W
+    the single-precision state and the df64 or the single-precision deviation
+    equilibrium."""
+    from paper_2502_16818_gb300 import CDBM_FP32_DEV, CDBM_FP32_DF64, CDBM_FP64, Solver, workloads as W
     runs = [("sod_500_I0", W.sod(nx=500, I=0.0), 10000), ("lax_2000_I0", W.lax(nx=2000, I=0.0), 10000)]
     runs += [("sound_512_I%d" % I, W.sound(n=512, I=float(I)), 2000) for I in (0, 1, 3)]
     res = {}
     for name, w, steps in runs:
         row = {"cells": w.nx * w.ny, "steps": steps}
-        for label, prec in (("fp64", CDBM_FP64), ("fp32_df64", CDBM_FP32_DF64)):
+        for label, prec in (("fp64", CDBM_FP64), ("fp32_df64", CDBM_FP32_DF64), ("fp32_dev", CDBM_FP32_DEV)):
             st = torch.cuda.Stream()
             with torch.cuda.stream(st):
                 s = Solver.from_workload(w, stream=st, precision=prec)

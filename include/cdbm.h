@@ -90,10 +90,21 @@ typedef enum {
                           /* conserved sums, the moment shift and the equilibrium  */
                           /* product in double; f_eq is rounded to single when it  */
                           /* enters the stage update                               */
-    CDBM_FP32_DF64 = 2    /* as CDBM_FP32_BULK, with the sums, moment shift and    */
+    CDBM_FP32_DF64 = 2,   /* as CDBM_FP32_BULK, with the sums, moment shift and    */
                           /* equilibrium product in double-float arithmetic (pairs */
                           /* of floats) on the FP32 pipe, with an absolute error   */
                           /* of a few 2^-47 of the reference equilibrium F         */
+    CDBM_FP32_DEV = 3     /* everything in IEEE single: the state as its deviation */
+                          /* from F and the equilibrium formed from the deviations */
+                          /* of the moments from F's (no value of the size of F    */
+                          /* enters a difference; the block product compensated;   */
+                          /* mass, momentum and energy projected back onto the     */
+                          /* cell's), with an error of a few 2^-24 of the          */
+                          /* deviation: as accurate as CDBM_FP32_BULK on flows     */
+                          /* near the reference state, 2-4x less on strong shocks  */
+                          /* (Sod, 10^4 steps: 2.1e-5 relative L2 density error).  */
+                          /* Not the FP64 moment shift and product of              */
+                          /* CDBM_FP32_BULK; grids only (the batch API refuses it) */
 } cdbm_precision;
 
 /* Time integrator.  The paper names a second-order Runge-Kutta scheme without
@@ -137,10 +148,11 @@ cdbm_status cdbm_init(cdbm_ctx *ctx, const double *rho, const double *ux, const 
  * fused Runge-Kutta stage kernels (rho, u, T -> f_eq -> BGK + NND transport of all
  * 16 velocities -> stage update).  Launches are replayed from a CUDA graph.  A 1-D
  * grid (ny = 1) small enough for one thread-block cluster (at most 16 x 64 cells for
- * CDBM_FP64, 16 x 256 for the single-precision states) instead runs all nsteps in
- * one persistent launch with its state in the cluster's shared memory; the results
- * are the same bit for bit for the single-precision states and the same to rounding
- * for CDBM_FP64, whose cluster kernel splits each cell over four threads.
+ * CDBM_FP64, 16 x 256 for CDBM_FP32_BULK and CDBM_FP32_DF64) instead runs all nsteps
+ * in one persistent launch with its state in the cluster's shared memory; the
+ * results are the same bit for bit for the single-precision states and the same to
+ * rounding for CDBM_FP64, whose cluster kernel splits each cell over four threads.
+ * CDBM_FP32_DEV steps every grid with the stage kernels.
  * Asynchronous; a non-physical state is reported by the next cdbm_sync.
  */
 cdbm_status cdbm_step(cdbm_ctx *ctx, int nsteps);
@@ -184,15 +196,15 @@ cdbm_status cdbm_tne(cdbm_ctx *ctx, double *out);
 cdbm_status cdbm_conserved_sums(cdbm_ctx *ctx, double out[4]);
 
 /* Copies the state f ([16][ny][nx] doubles, host or device) and the time out / in;
- * a single-precision state (CDBM_FP32_BULK, CDBM_FP32_DF64) is widened on the way
- * out and rounded on the way in. */
+ * a single-precision state (CDBM_FP32_BULK, CDBM_FP32_DF64, CDBM_FP32_DEV) is widened
+ * on the way out and rounded on the way in. */
 cdbm_status cdbm_get_state(cdbm_ctx *ctx, double *f, double *t);
 cdbm_status cdbm_set_state(cdbm_ctx *ctx, const double *f, double t);
 
 /* Device pointer of the state f ([16][ny][nx], owned by the context, valid until
  * cdbm_destroy; steps update it in place): doubles for CDBM_FP64, floats (the
- * deviation g = f - F from the reference equilibrium F) for CDBM_FP32_BULK and
- * CDBM_FP32_DF64. */
+ * deviation g = f - F from the reference equilibrium F) for CDBM_FP32_BULK,
+ * CDBM_FP32_DF64 and CDBM_FP32_DEV. */
 cdbm_status cdbm_state_ptr(cdbm_ctx *ctx, void **f);
 
 /* Simulated time (host scalar). */
@@ -272,7 +284,8 @@ void cdbm_destroy(cdbm_ctx *ctx);
  * requested steps; a block owns a fixed set of whole tubes, so blocks never wait on
  * one another (block barriers only, between Runge-Kutta stages).  The two-stage TVD
  * scheme is used.  Precision: CDBM_FP64, CDBM_FP32_BULK or CDBM_FP32_DF64 (single
- * precision with a per-tube reference F = f_eq of the tube's mean rho and T).
+ * precision with a per-tube reference F = f_eq of the tube's mean rho and T);
+ * CDBM_FP32_DEV is refused with CDBM_EINVAL.
  * ---------------------------------------------------------------------------- */
 typedef struct cdbm_batch cdbm_batch;
 

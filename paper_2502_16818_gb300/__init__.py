@@ -6,7 +6,7 @@ wrapper that takes device memory and streams from PyTorch.  ``workloads`` holds
 the seeded initial conditions of the paper's test problems.
 """
 from .cdbm import (BatchSolver, CdbmError, Solver, CDBM_BC_PERIODIC, CDBM_BC_ZEROGRAD, CDBM_FP64,  # noqa: F401
-                   CDBM_FP32_BULK, CDBM_FP32_DF64, CDBM_RK2_MIDPOINT, CDBM_RK2_TVD)
+                   CDBM_FP32_BULK, CDBM_FP32_DF64, CDBM_FP32_DEV, CDBM_RK2_MIDPOINT, CDBM_RK2_TVD)
 from . import workloads  # noqa: F401
 
 

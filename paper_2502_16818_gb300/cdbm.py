@@ -20,7 +20,7 @@ CDBM_OK, CDBM_EINVAL, CDBM_ESINGULAR, CDBM_ENOMEM, CDBM_ECUDA, CDBM_ENONPHYS, CD
 STATUS_NAMES = {0: "CDBM_OK", 1: "CDBM_EINVAL", 2: "CDBM_ESINGULAR", 3: "CDBM_ENOMEM",
                 4: "CDBM_ECUDA", 5: "CDBM_ENONPHYS", 6: "CDBM_ETIMEOUT"}
 CDBM_BC_PERIODIC, CDBM_BC_ZEROGRAD = 0, 1
-CDBM_FP64, CDBM_FP32_BULK, CDBM_FP32_DF64 = 0, 1, 2
+CDBM_FP64, CDBM_FP32_BULK, CDBM_FP32_DF64, CDBM_FP32_DEV = 0, 1, 2, 3
 CDBM_ADJ_LIMITER_EXACT, CDBM_ADJ_LIMITER_FROZEN_RATIO, CDBM_ADJ_LIMITER_FROZEN = 0, 1, 2
 CDBM_RK2_TVD, CDBM_RK2_MIDPOINT = 0, 1
 

@@ -358,6 +358,7 @@ void build_stages(cdbm_ctx *c)
         a.bc_x = c->grid.bc_x;
         a.bc_y = c->grid.bc_y;
         fill_df_consts(a);
+        fill_dev_proj(a, r.gamma * h);
         c->launch[s] = stage_launch_config(a, r.with_base, c->sm_count, c->precision, c->march_enabled,
                                            c->small_enabled);
     }
@@ -440,7 +441,8 @@ cdbm_status cdbm_create(const cdbm_grid *grid, const cdbm_vset *vset, double I, 
     if (!(std::isfinite(I) && I >= 0.0)) return create_err(CDBM_EINVAL, "I must be finite and >= 0");
     if ((grid->bc_x != 0 && grid->bc_x != 1) || (grid->bc_y != 0 && grid->bc_y != 1))
         return create_err(CDBM_EINVAL, "unknown boundary kind");
-    if (precision != CDBM_FP64 && precision != CDBM_FP32_BULK && precision != CDBM_FP32_DF64)
+    if (precision != CDBM_FP64 && precision != CDBM_FP32_BULK && precision != CDBM_FP32_DF64 &&
+        precision != CDBM_FP32_DEV)
         return create_err(CDBM_EINVAL, "unsupported precision %d", precision);
     for (int g = 0; g < 4; ++g)
         if (!std::isfinite(vset->v[g]) || !std::isfinite(vset->eta[g]) || vset->v[g] <= 0.0 ||

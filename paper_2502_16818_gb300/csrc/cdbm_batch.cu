@@ -638,7 +638,8 @@ cdbm_status cdbm_batch_create(int ntubes, const int *nx, const double *dx, const
         return bcreate_err(CDBM_EINVAL, "dt and tau must be finite and > 0");
     if (dt / tau > 2.0) return bcreate_err(CDBM_EINVAL, "dt/tau = %g exceeds 2", dt / tau);
     if (precision != CDBM_FP64 && precision != CDBM_FP32_BULK && precision != CDBM_FP32_DF64)
-        return bcreate_err(CDBM_EINVAL, "unsupported precision %d", precision);
+        return bcreate_err(CDBM_EINVAL, "unsupported precision %d (the batch takes CDBM_FP64, CDBM_FP32_BULK "
+                                        "and CDBM_FP32_DF64)", precision);
     double vmax = 0.0;
     for (int g = 0; g < 4; ++g) {
         if (!std::isfinite(vset->v[g]) || !std::isfinite(vset->eta[g]) || vset->v[g] <= 0 || vset->eta[g] < 0)

@@ -86,6 +86,18 @@ using DFModel = DFModelT<float>;
 using DFShift = DFShiftT<float>;
 using DFConsts = DFConstsT<float>;
 
+// Conservation projection of the single-precision deviation equilibrium
+// (CDBM_FP32_DEV): the group rest values s_g and odd components (cx, cy)_g are
+// corrected by alpha + beta w_g and c_g (gamma_x, gamma_y) so that the equilibrium's
+// mass, momentum and energy equal gamma h times the cell's; the corrections solve
+// [16, 4 sum w; 4 sum w, 4 sum w^2] (alpha, beta) = residuals and gamma = residual /
+// sum_i c_ix^2.
+struct DevProj {
+    float gh;             // gamma h of the stage
+    float a00, a01, a11;  // inverse of the 2 x 2 matrix above
+    float rkc;            // 1 / sum_i c_ix^2
+};
+
 // One Runge-Kutta stage: out = a_base * base + a_self * g + eq(g) - sum_r l_r D_r(g),
 // i.e. alpha f^n + beta g + gamma dt L(g) with a_self = beta - gamma h, the
 // equilibrium blocks scaled by gamma h and l = gamma dt c_g / dr.
@@ -110,8 +122,9 @@ struct StageArgs {
     // ny = 1).  The frozen-limiter adjoint stage uses them to fold -l o_m into the
     // self term.
     double a_self_x[4], a_self_y[4], a_self_xy[4];
-    DFConsts d;                   // df64 copies (CDBM_FP32_DF64)
+    DFConsts d;                   // df64 copies (CDBM_FP32_DF64; their high parts for CDBM_FP32_DEV)
     DFConstsT<float2> d2;         // the same, each value twice (two-column kernel)
+    DevProj dp;                   // conservation projection (CDBM_FP32_DEV)
     float2 a_base_f2, a_self_f2;  // a_base_f, a_self_f, lx_f, ly_f twice
     float2 lx_f2[4], ly_f2[4];
     int nx, ny;
@@ -142,7 +155,7 @@ constexpr size_t kThreadErrorBytes = 256;
 char *thread_error_buffer();
 
 // ---- launchers (cdbm_kernels.cu); each returns the launch error ----
-// `prec` is the precision mode (CDBM_FP64, CDBM_FP32_BULK or CDBM_FP32_DF64), which
+// `prec` is the precision mode (CDBM_FP64, CDBM_FP32_BULK, CDBM_FP32_DF64 or CDBM_FP32_DEV), which
 // sets the storage of the distribution buffers; fields, Delta* and sums are always
 // double.
 cudaError_t launch_init(const FieldArgs &a, const double *rho, const double *ux,
@@ -208,7 +221,7 @@ cudaError_t launch_macros_vjp(const FieldArgs &a, const double *f, const double 
 cudaError_t launch_sum(const double *v, int n, double *out, cudaStream_t s);
 
 // Single-precision storage (FP32 bulk, with the equilibrium in double or in df64).
-inline bool single_storage(int prec) { return prec == CDBM_FP32_BULK || prec == CDBM_FP32_DF64; }
+inline bool single_storage(int prec) { return prec == CDBM_FP32_BULK || prec == CDBM_FP32_DF64 || prec == CDBM_FP32_DEV; }
 // Bytes of one distribution value in storage precision `prec`.
 inline size_t storage_bytes(int prec) { return single_storage(prec) ? 4 : 8; }
 // Double-float copies of double constants (host side, cdbm_kernels.cu).
@@ -217,6 +230,8 @@ DFModel df_model(const ModelConsts &m);
 DFShift df_shift(const double sF[4], double rhoF, double EF);
 // Fills a.d from the double constants of a.
 void fill_df_consts(StageArgs &a);
+// The conservation projection of a stage whose blocks are scaled by gh = gamma h.
+void fill_dev_proj(StageArgs &a, double gh);
 // The same constants with each value twice, for the two-column (packed FP32x2) kernels.
 DFBlocksT<float2> df_blocks_twice(const DFBlocks &d);
 DFModelT<float2> df_model_twice(const DFModel &d);

@@ -1,15 +1,16 @@
 // CDBM kernels: initial equilibrium, the fused Runge-Kutta stage, macroscopic
 // fields, nonequilibrium moments and conserved sums.  The distribution buffers
-// are stored in double (CDBM_FP64) or single (CDBM_FP32_BULK, CDBM_FP32_DF64)
-// precision, selected by the template parameter TS; the conserved sums and the
-// equilibrium of a stage are computed in double, or in double-float arithmetic
-// on the FP32 pipe for CDBM_FP32_DF64 (template flag kDF).
+// are stored in double (CDBM_FP64) or single (CDBM_FP32_BULK, CDBM_FP32_DF64,
+// CDBM_FP32_DEV) precision, selected by the template parameter TS; the conserved
+// sums and the equilibrium of a stage are computed in double, in double-float
+// arithmetic on the FP32 pipe for CDBM_FP32_DF64, or in single precision on the
+// moment deviations for CDBM_FP32_DEV (template parameter kEq).
 //
 // Layout: f[16][ny][nx] (velocity plane outermost, x fastest).  A block covers a
 // run of columns along x, so centre loads and stores of a warp are coalesced rows
 // and the stencil neighbours (x +- 1, 2 and the rows y +- 1, 2) are served from
 // L1/L2 or shared memory.  stage_kernel gives each thread one cell; the
-// row-marching kernels give each thread one column (two for the df64 state) over a
+// row-marching kernels give each thread one column (two for the df64 and deviation states) over a
 // run of rows.
 #include "cdbm_stage.cuh"
 
@@ -28,7 +29,7 @@ constexpr int kStageThreads = 128;
 #ifndef CDBM_STAGE_MIN_BLOCKS_DF
 #define CDBM_STAGE_MIN_BLOCKS_DF 6
 #endif
-constexpr int stage_min_blocks(bool df) { return df ? CDBM_STAGE_MIN_BLOCKS_DF : CDBM_STAGE_MIN_BLOCKS; }
+constexpr int stage_min_blocks(int eq) { return eq != kEqDouble ? CDBM_STAGE_MIN_BLOCKS_DF : CDBM_STAGE_MIN_BLOCKS; }
 
 // ---------------------------------------------------------------- init (K0)
 
@@ -66,8 +67,8 @@ __global__ void __launch_bounds__(128) init_kernel(const FieldArgs a, const doub
 
 // out = a_base base + a_self g + gamma h f_eq(g) - sum_r l_r D_r(g) for one cell:
 // macros -> equilibrium -> BGK -> NND transport of all 16 velocities -> update.
-template <typename TS, bool kBase, bool kFlatY, bool kDF>
-__global__ void __launch_bounds__(kStageThreads, stage_min_blocks(kDF))
+template <typename TS, bool kBase, bool kFlatY, int kEq>
+__global__ void __launch_bounds__(kStageThreads, stage_min_blocks(kEq))
     stage_kernel(const TS *__restrict__ g, const TS *base, TS *out, const StageArgs a, unsigned *flag)
 {
     const int nx = a.nx, ny = a.ny;
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(kStageThreads, stage_min_blocks(kDF))
 #pragma unroll
         for (int i = 0; i < kNV; ++i) fs[i] = __ldg(g + i * P + c);
         TS heq[kNV];
-        stage_equilibrium<TS, kDF>(a, fs, heq, flag);
+        stage_equilibrium<TS, kEq>(a, fs, heq, flag);
 
 #pragma unroll
         for (int i = 0; i < kNV; ++i) {
@@ -130,8 +131,8 @@ __host__ __device__ constexpr int yvel(int k)       // k-th velocity with diry !
     return k < 2 ? 1 + 2 * k : (k < 6 ? k + 2 : (k < 8 ? 9 + 2 * (k - 6) : k + 4));
 }
 
-template <typename TS, bool kBase, bool kDF>
-__global__ void __launch_bounds__(kStageThreads, stage_min_blocks(kDF))
+template <typename TS, bool kBase, int kEq>
+__global__ void __launch_bounds__(kStageThreads, stage_min_blocks(kEq))
     stage_march_kernel(const TS *__restrict__ g, const TS *base, TS *out, const StageArgs a, unsigned *flag)
 {
     // In double precision the x differences are shared as well: each thread computes
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(kStageThreads, stage_min_blocks(kDF))
 #pragma unroll
             for (int i = 0; i < kNV; ++i) fs[i] = __ldg(g + i * P + c);
             TS heq[kNV];
-            stage_equilibrium<TS, kDF>(a, fs, heq, flag);
+            stage_equilibrium<TS, kEq>(a, fs, heq, flag);
             int k = 0;
 #pragma unroll
             for (int i = 0; i < kNV; ++i) {
@@ -324,7 +325,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <bool kBase, bool kVec>
+template <bool kBase, bool kVec, int kEq>
 __global__ void __launch_bounds__(kStageThreads, kMarch2MinBlocks)
     stage_march2_kernel(const float *__restrict__ g, const float *base, float *out, const StageArgs a,
                         unsigned *flag)
@@ -417,7 +418,21 @@ __global__ void __launch_bounds__(kStageThreads, kMarch2MinBlocks)
         float2 fs[kNV], o[kNV], heq[kNV];
 #pragma unroll
         for (int i = 0; i < kNV; ++i) fs[i] = staged_at(b, i);
-        df_equilibrium(a.d2.b, a.d2.m, a.d2.r, fs, heq, flag);
+        if constexpr (kEq == kEqF32) {
+            // one column at a time (see cdbm_f32dev.cuh)
+            float fa[kNV], fb[kNV], ha[kNV], hb[kNV];
+#pragma unroll
+            for (int i = 0; i < kNV; ++i) {
+                fa[i] = fs[i].x;
+                fb[i] = fs[i].y;
+            }
+            f32_equilibrium(a.d.b, a.d.m, a.d.r, a.dp, fa, ha, flag);
+            f32_equilibrium(a.d.b, a.d.m, a.d.r, a.dp, fb, hb, flag);
+#pragma unroll
+            for (int i = 0; i < kNV; ++i) heq[i] = make_float2(ha[i], hb[i]);
+        } else {
+            df_equilibrium(a.d2.b, a.d2.m, a.d2.r, fs, heq, flag);
+        }
 #pragma unroll
         for (int i = 0; i < kNV; ++i) {
             o[i] = fma_rn(a.a_self_f2, fs[i], heq[i]);
@@ -779,22 +794,29 @@ unsigned grid_for(size_t cells, int threads)
     return (unsigned)(b < 1 ? 1 : (b > 1048576 ? 1048576 : b));
 }
 
-void *stage_march2_func(bool with_base, bool vec)
+template <int kEq>
+void *stage_march2_func_t(bool with_base, bool vec)
 {
-    if (with_base) return vec ? (void *)stage_march2_kernel<true, true> : (void *)stage_march2_kernel<true, false>;
-    return vec ? (void *)stage_march2_kernel<false, true> : (void *)stage_march2_kernel<false, false>;
+    if (with_base)
+        return vec ? (void *)stage_march2_kernel<true, true, kEq> : (void *)stage_march2_kernel<true, false, kEq>;
+    return vec ? (void *)stage_march2_kernel<false, true, kEq> : (void *)stage_march2_kernel<false, false, kEq>;
 }
 
-template <typename TS, bool kDF>
+void *stage_march2_func(bool with_base, bool vec, bool dev)
+{
+    return dev ? stage_march2_func_t<kEqF32>(with_base, vec) : stage_march2_func_t<kEqDF>(with_base, vec);
+}
+
+template <typename TS, int kEq>
 void *stage_func(bool march, bool with_base, bool flat)
 {
-    if constexpr (!kDF) {   // the df64 state marches with stage_march2_kernel
+    if constexpr (kEq == kEqDouble) {   // the single-precision equilibria march with stage_march2_kernel
         if (march)
-            return with_base ? (void *)stage_march_kernel<TS, true, false> : (void *)stage_march_kernel<TS, false, false>;
+            return with_base ? (void *)stage_march_kernel<TS, true, kEq> : (void *)stage_march_kernel<TS, false, kEq>;
     }
     if (with_base)
-        return flat ? (void *)stage_kernel<TS, true, true, kDF> : (void *)stage_kernel<TS, true, false, kDF>;
-    return flat ? (void *)stage_kernel<TS, false, true, kDF> : (void *)stage_kernel<TS, false, false, kDF>;
+        return flat ? (void *)stage_kernel<TS, true, true, kEq> : (void *)stage_kernel<TS, true, false, kEq>;
+    return flat ? (void *)stage_kernel<TS, false, true, kEq> : (void *)stage_kernel<TS, false, false, kEq>;
 }
 
 }  // namespace
@@ -889,8 +911,9 @@ StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count
         L.grid = dim3((unsigned)((4 * (size_t)a.nx + kSplitFlatThreads - 1) / kSplitFlatThreads), 1, 1);
         return L;
     }
-    // The df64 state marches two columns per thread (stage_march2_kernel).
-    const bool pair = prec == CDBM_FP32_DF64;
+    // The df64 and single-precision deviation equilibria march two columns per thread
+    // (stage_march2_kernel).
+    const bool pair = prec == CDBM_FP32_DF64 || prec == CDBM_FP32_DEV;
     const int cols = pair ? 2 * kStageThreads : kStageThreads;
     const unsigned xblocks = (unsigned)((a.nx + cols - 1) / cols);
     // Row-marching kernel when runs of at least 8 rows still give two full waves of
@@ -898,7 +921,7 @@ StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count
     // (a 512^2 sound wave has 4 blocks across) runs of 4 or 2 rows are used if they
     // give two waves: each run repeats a 2-row prologue, but the x and y differences
     // are still computed once per cell.
-    const size_t wave = (size_t)sm_count * (pair ? kMarch2MinBlocks : stage_min_blocks(false));
+    const size_t wave = (size_t)sm_count * (pair ? kMarch2MinBlocks : stage_min_blocks(kEqDouble));
     int R = 8;
     while (R < 32 && (size_t)xblocks * ((a.ny + 2 * R - 1) / (2 * R)) >= 8 * wave) R *= 2;
     bool march = allow_march && !flat && a.ny >= 16 && (size_t)xblocks * ((a.ny + 7) / 8) >= 2 * wave;
@@ -909,9 +932,9 @@ StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count
         }
     }
     if (march) {
-        L.func = pair ? stage_march2_func(with_base, (a.nx & 1) == 0)
-                 : prec == CDBM_FP32_BULK ? stage_func<float, false>(true, with_base, false)
-                                          : stage_func<double, false>(true, with_base, false);
+        L.func = pair ? stage_march2_func(with_base, (a.nx & 1) == 0, prec == CDBM_FP32_DEV)
+                 : prec == CDBM_FP32_BULK ? stage_func<float, kEqDouble>(true, with_base, false)
+                                          : stage_func<double, kEqDouble>(true, with_base, false);
         if (prec == CDBM_FP64) {
             // the double-buffered x row buffer of stage_march_kernel<double>
             L.smem = kMarchRowBytes;
@@ -931,9 +954,10 @@ StageLaunch stage_launch_config(const StageArgs &a, bool with_base, int sm_count
         L.grid = dim3(xblocks, yblocks < 65535 ? yblocks : 65535, 1);
         return L;
     }
-    L.func = prec == CDBM_FP32_DF64   ? stage_func<float, true>(false, with_base, flat)
-             : prec == CDBM_FP32_BULK ? stage_func<float, false>(false, with_base, flat)
-                                      : stage_func<double, false>(false, with_base, flat);
+    L.func = prec == CDBM_FP32_DEV    ? stage_func<float, kEqF32>(false, with_base, flat)
+             : prec == CDBM_FP32_DF64 ? stage_func<float, kEqDF>(false, with_base, flat)
+             : prec == CDBM_FP32_BULK ? stage_func<float, kEqDouble>(false, with_base, flat)
+                                      : stage_func<double, kEqDouble>(false, with_base, flat);
     // Small grids: narrower blocks so that more SMs share the cells.
     int threads = kStageThreads;
     while (threads > 32 && cells < (size_t)sm_count * threads * 2) threads >>= 1;
@@ -1042,6 +1066,22 @@ void fill_df_consts(StageArgs &a)
         a.lx_f2[g] = make_float2(a.lx_f[g], a.lx_f[g]);
         a.ly_f2[g] = make_float2(a.ly_f[g], a.ly_f[g]);
     }
+}
+
+void fill_dev_proj(StageArgs &a, double gh)
+{
+    double sw = 0.0, sw2 = 0.0, kc = 0.0;
+    for (int g = 0; g < 4; ++g) {
+        sw += a.m.w[g];
+        sw2 += a.m.w[g] * a.m.w[g];
+        kc += ((g & 1) == 0 ? 2.0 : 4.0) * a.m.c[g] * a.m.c[g];    // sum_i c_ix^2 over the group
+    }
+    const double m00 = 16.0, m01 = 4.0 * sw, m11 = 4.0 * sw2, det = m00 * m11 - m01 * m01;
+    a.dp.gh = (float)gh;
+    a.dp.a00 = (float)(m11 / det);
+    a.dp.a01 = (float)(-m01 / det);
+    a.dp.a11 = (float)(m00 / det);
+    a.dp.rkc = (float)(1.0 / kc);
 }
 
 cudaError_t launch_stage(const StageLaunch &L, const void *g, const void *base, void *out,

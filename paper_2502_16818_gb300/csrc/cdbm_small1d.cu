@@ -37,11 +37,11 @@ __device__ __forceinline__ TS cluster_value(const cg::cluster_group &cl, const T
 }
 
 // One stage over this CTA's cells: dst = a_base base + a_self src + gamma h f_eq(src)
-// - sum l D(src), the operations of stage_kernel<TS, kBase, true, kDF> per cell.  All
+// - sum l D(src), the operations of stage_kernel<TS, kBase, true, kEq> per cell.  All
 // stencil values (and the base) are gathered into registers before the first store,
 // so the loads of the edge cells from the neighbouring CTAs overlap instead of each
 // waiting behind a store the compiler cannot prove independent.
-template <typename TS, bool kBase, bool kDF>
+template <typename TS, bool kBase, int kEq>
 __device__ __forceinline__ void cluster_stage(const cg::cluster_group &cl, const TS *src, const TS *base, TS *dst,
                                               const StageArgs &a, int chunk, int rank, int x0, int len,
                                               unsigned *flag)
@@ -81,7 +81,7 @@ __device__ __forceinline__ void cluster_stage(const cg::cluster_group &cl, const
             }
         }
         TS heq[kNV];
-        stage_equilibrium<TS, kDF>(a, fs, heq, flag);
+        stage_equilibrium<TS, kEq>(a, fs, heq, flag);
         int k = 0;
 #pragma unroll
         for (int i = 0; i < kNV; ++i) {
@@ -96,7 +96,7 @@ __device__ __forceinline__ void cluster_stage(const cg::cluster_group &cl, const
     }
 }
 
-template <typename TS, bool kDF>
+template <typename TS, int kEq>
 __global__ void __launch_bounds__(256) small1d_kernel(TS *f, int nsteps, const StageArgs a0, const StageArgs a1,
                                                       unsigned *flag, int chunk)
 {
@@ -114,9 +114,9 @@ __global__ void __launch_bounds__(256) small1d_kernel(TS *f, int nsteps, const S
     }
     cl.sync();
     for (int s = 0; s < nsteps; ++s) {
-        cluster_stage<TS, false, kDF>(cl, s0, nullptr, s1, a0, chunk, rank, x0, len, flag);
+        cluster_stage<TS, false, kEq>(cl, s0, nullptr, s1, a0, chunk, rank, x0, len, flag);
         cl.sync();
-        cluster_stage<TS, true, kDF>(cl, s1, s0, s0, a1, chunk, rank, x0, len, flag);
+        cluster_stage<TS, true, kEq>(cl, s1, s0, s0, a1, chunk, rank, x0, len, flag);
         cl.sync();
     }
     for (int k = threadIdx.x; k < kNV * len; k += blockDim.x) {
@@ -419,16 +419,17 @@ __global__ void __launch_bounds__(256) small1d_split_df_kernel(float *f, int nst
     }
 }
 
-template <typename TS, bool kDF>
-void *small1d_func() { return (void *)small1d_kernel<TS, kDF>; }
+template <typename TS, int kEq>
+void *small1d_func() { return (void *)small1d_kernel<TS, kEq>; }
 
 constexpr int kSplitDfMaxChunk = 128;     // two threads per cell within 256 threads
 
 void *small1d_func_of(int prec, int chunk)
 {
     if (prec == CDBM_FP32_DF64)
-        return chunk <= kSplitDfMaxChunk ? (void *)small1d_split_df_kernel : small1d_func<float, true>();
-    if (prec == CDBM_FP32_BULK) return small1d_func<float, false>();
+        return chunk <= kSplitDfMaxChunk ? (void *)small1d_split_df_kernel : small1d_func<float, kEqDF>();
+    if (prec == CDBM_FP32_DEV) return small1d_func<float, kEqF32>();
+    if (prec == CDBM_FP32_BULK) return small1d_func<float, kEqDouble>();
     return (void *)small1d_split_kernel;
 }
 

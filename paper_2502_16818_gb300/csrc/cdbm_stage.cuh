@@ -2,7 +2,7 @@
 // coefficients in the storage precision and the scaled equilibrium of one cell.
 #pragma once
 
-#include "cdbm_df64.cuh"
+#include "cdbm_f32dev.cuh"
 
 namespace cdbm {
 
@@ -28,14 +28,22 @@ __device__ __forceinline__ TS ly_of(const StageArgs &a, int g)
     if constexpr (kSingle<TS>) return a.ly_f[g]; else return a.ly[g];
 }
 
+// How a stage forms the equilibrium: in double (CDBM_FP64, CDBM_FP32_BULK), in df64
+// (CDBM_FP32_DF64) or in single precision on the deviations (CDBM_FP32_DEV).
+constexpr int kEqDouble = 0, kEqDF = 1, kEqF32 = 2;
+
 // gamma h f_eq of one cell in the storage precision (minus gamma h F for the
 // single-precision deviation state): moments, primitives and equilibrium in double,
-// or all of it in df64 when kDF.
-template <typename TS, bool kDF>
+// all of it in df64 (kEq = kEqDF) or in single precision on the moment deviations
+// (kEq = kEqF32).
+template <typename TS, int kEq>
 __device__ __forceinline__ void stage_equilibrium(const StageArgs &a, const TS fs[kNV], TS heq[kNV],
                                                   unsigned *flag)
 {
-    if constexpr (kDF) {
+    if constexpr (kEq == kEqF32) {
+        static_assert(kSingle<TS>, "the deviation equilibrium is for the single-precision state");
+        f32_equilibrium(a.d.b, a.d.m, a.d.r, a.dp, fs, heq, flag);
+    } else if constexpr (kEq == kEqDF) {
         static_assert(kSingle<TS>, "df64 equilibrium is for the single-precision state");
         df_equilibrium(a.d.b, a.d.m, a.d.r, fs, heq, flag);
     } else {

@@ -32,7 +32,7 @@ def test_bench_line_has_the_contract_keys():
     d = json.loads(lines[0])
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
                 "vs_baseline", "dtype", "data", "config", "gpu_launches", "clocks", "roofline", "e2e",
-                "cpu_baseline", "fp32_bulk", "fp32_df64"):
+                "cpu_baseline", "fp32_bulk", "fp32_df64", "fp32_dev"):
         assert key in d, key
     assert d["steps"] == 4 and d["warmup"] == 3 and d["n_gpus"] == 1
     cells = 256 * 256
@@ -50,11 +50,11 @@ def test_bench_line_has_the_contract_keys():
     assert e2e["h2d_bytes_per_step"] > 0 and e2e["d2h_bytes_per_step"] > 0 and e2e["value"] > 0
     cpu = d["cpu_baseline"]
     assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] > 0
-    for mode in ("fp32_bulk", "fp32_df64"):
+    for mode in ("fp32_bulk", "fp32_df64", "fp32_dev"):
         assert d[mode]["l2_density_error_vs_fp64"] <= 1e-5
     # the on-demand kernels, each with its time and HBM GB/s
     names = {"fp64": ("init_kernel", "macros_kernel", "tne_kernel", "sums_partial_kernel")}
-    names["fp32_bulk"] = names["fp32_df64"] = names["fp64"][1:]
+    names["fp32_bulk"] = names["fp32_df64"] = names["fp32_dev"] = names["fp64"][1:]
     for mode, keys in names.items():
         aux = d["aux_kernels"] if mode == "fp64" else d[mode]["aux_kernels"]
         assert sorted(aux) == sorted(keys), (mode, sorted(aux))

@@ -27,8 +27,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 FIELDS = ("rho", "ux", "uy", "T")
-PRECISIONS = [0, 1, 2]
-PREC_IDS = ["fp64", "fp32_bulk", "fp32_df64"]
+PRECISIONS = [0, 1, 2, 3]
+PREC_IDS = ["fp64", "fp32_bulk", "fp32_df64", "fp32_dev"]
 
 
 @pytest.fixture(scope="module", autouse=True)

@@ -430,7 +430,7 @@ def test_macros_roundtrip_extreme_density():
     np.testing.assert_allclose(got[3], w.T, rtol=1e-13)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("rk", [0, 1])
 @pytest.mark.parametrize("bc", [W.ZERO_GRADIENT, W.PERIODIC])
 def test_small_grid_cluster_path_matches_stage_launches(prec, rk, bc):
@@ -467,7 +467,7 @@ def test_small_grid_cluster_path_matches_stage_launches(prec, rk, bc):
             assert np.array_equal(states[0], states[1]), (nx, prec, rk, bc)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 @pytest.mark.parametrize("shape", [(1026, 600), (1027, 600), (514, 2100), (3, 4096), (2, 4096)])
 @pytest.mark.parametrize("bc", [(W.PERIODIC, W.PERIODIC), (W.ZERO_GRADIENT, W.ZERO_GRADIENT)])
 def test_row_marching_matches_one_cell_per_thread(prec, shape, bc):
