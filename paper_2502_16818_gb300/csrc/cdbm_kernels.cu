@@ -418,6 +418,20 @@ __global__ void __launch_bounds__(kStageThreads, kMarch2MinBlocks)
         float2 fs[kNV], o[kNV], heq[kNV];
 #pragma unroll
         for (int i = 0; i < kNV; ++i) fs[i] = staged_at(b, i);
+        // The deviation equilibrium leaves registers free: its x neighbour pairs are
+        // loaded before it, so that their latency overlaps its arithmetic (1.37 ->
+        // 1.34 ms per 4096^2 step; the df64 equilibrium has no registers to spare).
+        constexpr bool kEarlyX = kVec && kEq == kEqF32;
+        float2 nl[kNV], nr[kNV];
+        if constexpr (kEarlyX) {
+#pragma unroll
+            for (int i = 0; i < kNV; ++i) {
+                if (dirx(i) != 0) {
+                    nl[i] = ld_left(g + i * P + row);
+                    nr[i] = ld_right(g + i * P + row);
+                }
+            }
+        }
         if constexpr (kEq == kEqF32) {
             // one column at a time (see cdbm_f32dev.cuh)
             float fa[kNV], fb[kNV], ha[kNV], hb[kNV];
@@ -443,7 +457,14 @@ __global__ void __launch_bounds__(kStageThreads, kMarch2MinBlocks)
                 float2 u2, u1, d1;
                 if constexpr (kVec) {
                     // the pair's own cells stand in for the neighbours inside the pair
-                    const float2 L = ld_left(gp), Rr = ld_right(gp);
+                    float2 L, Rr;
+                    if constexpr (kEarlyX) {
+                        L = nl[i];
+                        Rr = nr[i];
+                    } else {
+                        L = ld_left(gp);
+                        Rr = ld_right(gp);
+                    }
                     u2 = pos ? L : Rr;
                     u1 = pos ? make_float2(L.y, fs[i].x) : make_float2(fs[i].y, Rr.x);
                     d1 = pos ? make_float2(fs[i].y, Rr.x) : make_float2(L.y, fs[i].x);
