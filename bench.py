@@ -511,13 +511,15 @@ def full_length_vortex(a, w, torch, Solver):
 
 def ensemble(a, torch):
     """1024 shock tubes, Nx ~ U{200..4000} (seed 0), one persistent autotuned launch
-    per call, FP64, FP32-bulk and FP32 with the df64 equilibrium; against a per-tube
+    per call, FP64, FP32-bulk, FP32 with the df64 equilibrium and FP32 with the
+    single-precision deviation equilibrium; against a per-tube
     loop of the single-grid FP64 solver over the same tubes."""
     from paper_2502_16818_gb300 import BatchSolver, Solver, workloads as W
     specs = W.ensemble_draw(1024, seed=0)
     tubes = [W.ensemble_tube(sp, steps=1000) for sp in specs]
     res = {"tubes": len(tubes), "cells": int(sum(w.nx for w in tubes)), "steps": a.ens_steps}
-    for name, prec in (("fp64_batched", 0), ("fp32_bulk_batched", 1), ("fp32_df64_batched", 2)):
+    for name, prec in (("fp64_batched", 0), ("fp32_bulk_batched", 1), ("fp32_df64_batched", 2),
+                       ("fp32_dev_batched", 3)):
         st = torch.cuda.Stream()
         b = BatchSolver(tubes, precision=prec, stream=st)
         b.init(tubes)

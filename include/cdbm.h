@@ -104,7 +104,7 @@ typedef enum {
                           /* near the reference state, 2-4x less on strong shocks  */
                           /* (Sod, 10^4 steps: 2.1e-5 relative L2 density error).  */
                           /* Not the FP64 moment shift and product of              */
-                          /* CDBM_FP32_BULK; grids only (the batch API refuses it) */
+                          /* CDBM_FP32_BULK                                        */
 } cdbm_precision;
 
 /* Time integrator.  The paper names a second-order Runge-Kutta scheme without
@@ -283,9 +283,8 @@ void cdbm_destroy(cdbm_ctx *ctx);
  * [16][total_cells].  One persistent kernel advances every tube through all
  * requested steps; a block owns a fixed set of whole tubes, so blocks never wait on
  * one another (block barriers only, between Runge-Kutta stages).  The two-stage TVD
- * scheme is used.  Precision: CDBM_FP64, CDBM_FP32_BULK or CDBM_FP32_DF64 (single
- * precision with a per-tube reference F = f_eq of the tube's mean rho and T);
- * CDBM_FP32_DEV is refused with CDBM_EINVAL.
+ * scheme is used.  Precision: any cdbm_precision (the single-precision states with a
+ * per-tube reference F = f_eq of the tube's mean rho and T).
  * ---------------------------------------------------------------------------- */
 typedef struct cdbm_batch cdbm_batch;
 

@@ -20,7 +20,7 @@
 #include <numeric>
 #include <vector>
 
-#include "cdbm_df64.cuh"
+#include "cdbm_stage.cuh"
 #include "cdbm_internal.h"
 
 using namespace cdbm;
@@ -39,7 +39,7 @@ struct TubeInfo {
     double sF[2][4];                  // per stage: gamma h F_g (FP32-bulk reference)
     double Fg[4];                     // reference equilibrium per group
     double rhoF, EF;                  // its conserved moments
-    DFShift dfs[2];                   // per stage: the same in df64 (CDBM_FP32_DF64)
+    DFShift dfs[2];                   // per stage: the same in df64 (CDBM_FP32_DF64, CDBM_FP32_DEV)
     DFShiftT<float2> dfs2[2];         // dfs with each value twice
 };
 
@@ -47,10 +47,11 @@ struct ClassConsts {
     EqBlocks eq[2];                   // per stage, scaled by gamma h
     EqBlocks unit;                    // unscaled (initialisation, macros)
     ModelConsts m;
-    DFBlocks dfeq[2];                 // eq[] and m in df64 (CDBM_FP32_DF64)
+    DFBlocks dfeq[2];                 // eq[] and m in df64 (CDBM_FP32_DF64; their high parts for CDBM_FP32_DEV)
     DFModel dfm;
     DFBlocksT<float2> dfeq2[2];       // the same with each value twice
     DFModelT<float2> dfm2;
+    DevProj dp[2];                    // per stage: conservation projection (CDBM_FP32_DEV)
 };
 
 struct BatchArgs {
@@ -85,13 +86,14 @@ __device__ __forceinline__ void load_state(const TS *g, long long P, int x, TS f
 // One Runge-Kutta stage (kStage 0 or 1) over the nx cells of one tube by the calling
 // block.  g, base and out point at the tube's first cell; planes are P apart.  The
 // arithmetic per cell is the flat (Ny = 1) stage of the single-grid kernels, with the
-// equilibrium in double or, with kDF, in df64.  Plain loads: the buffers are written
+// equilibrium in double, in df64 (kEq = kEqDF) or in single precision on the moment
+// deviations (kEqF32).  Plain loads: the buffers are written
 // inside this kernel, so the read-only path may not be used.
 // With kSym the tube's state is y-symmetric (conserved_sym): only the 10 distinct
 // velocities are loaded and computed, each result is stored to its plane and to the
 // plane of its mirror image, and the equilibrium drops the terms of j_y = 0.  The
 // values are those of the general form.
-template <typename TS, int kStage, bool kDF, bool kSym = false>
+template <typename TS, int kStage, int kEq, bool kSym = false>
 __device__ __forceinline__ void tube_stage(const TS *g, const TS *base, TS *out, long long P,
                                            const TubeInfo &t, const ClassConsts &C, TS a_self, TS a_base,
                                            unsigned *flag)
@@ -106,7 +108,10 @@ __device__ __forceinline__ void tube_stage(const TS *g, const TS *base, TS *out,
         TS fs[kNV];
         load_state<TS, kSym>(g, P, x, fs);
         TS heq[kNV];
-        if constexpr (kDF) {
+        if constexpr (kEq == kEqF32) {
+            // all 16 values (a symmetric state holds its mirror images in fs)
+            f32_equilibrium(C.dfeq[kStage], C.dfm, t.dfs[kStage], C.dp[kStage], fs, heq, flag);
+        } else if constexpr (kEq == kEqDF) {
             static_assert(kSingle<TS>, "df64 equilibrium is for the single-precision state");
             if constexpr (kSym) df_equilibrium_sym(C.dfeq[kStage], C.dfm, t.dfs[kStage], fs, heq, flag);
             else df_equilibrium(C.dfeq[kStage], C.dfm, t.dfs[kStage], fs, heq, flag);
@@ -304,14 +309,17 @@ __device__ __forceinline__ void tube_stage2(const float *g, const float *base, f
 // forms keep less live state: 512 for FP64 and FP32_BULK (126 / 116 registers at
 // 128 threads, no spills; 1.97e9 / 3.05e9 against 1.95e9 / 2.90e9 cell-updates/s on
 // the 1024-tube ensemble) and 640 for df64 (96 registers; 1.13e10 against 1.07e10).
-constexpr int batch_thread_budget(bool df, bool sym) { return sym ? (df ? 640 : 512) : 384; }
-constexpr int batch_min_blocks(int threads, bool df, bool sym)
+constexpr int batch_thread_budget(int eq, bool sym)
 {
-    return batch_thread_budget(df, sym) / threads > 0 ? batch_thread_budget(df, sym) / threads : 1;
+    return eq == kEqF32 ? 512 : (sym ? (eq == kEqDF ? 640 : 512) : 384);
+}
+constexpr int batch_min_blocks(int threads, int eq, bool sym)
+{
+    return batch_thread_budget(eq, sym) / threads > 0 ? batch_thread_budget(eq, sym) / threads : 1;
 }
 
-template <typename TS, int kThreads, bool kDF, bool kSym>
-__global__ void __launch_bounds__(kThreads, batch_min_blocks(kThreads, kDF, kSym)) batch_kernel(TS *f, TS *f1, const TubeInfo *tubes,
+template <typename TS, int kThreads, int kEq, bool kSym>
+__global__ void __launch_bounds__(kThreads, batch_min_blocks(kThreads, kEq, kSym)) batch_kernel(TS *f, TS *f1, const TubeInfo *tubes,
                                                          const int *work, const int *work_off, int nsteps,
                                                          const BatchArgs a, unsigned *flag)
 {
@@ -329,14 +337,14 @@ __global__ void __launch_bounds__(kThreads, batch_min_blocks(kThreads, kDF, kSym
                 tube_stage_shared_x<0, kThreads, kSym>(ft, nullptr, f1t, a.P, t, C, as0, ab0, flag, row_u);
                 __syncthreads();
                 tube_stage_shared_x<1, kThreads, kSym>(f1t, ft, ft, a.P, t, C, as1, ab1, flag, row_u);
-            } else if constexpr (kDF) {
+            } else if constexpr (kEq == kEqDF) {
                 tube_stage2<0, kSym>(ft, nullptr, f1t, a.P, t, C, a.a_self_f2[0], a.a_base_f2[0], flag);
                 __syncthreads();
                 tube_stage2<1, kSym>(f1t, ft, ft, a.P, t, C, a.a_self_f2[1], a.a_base_f2[1], flag);
             } else {
-                tube_stage<TS, 0, kDF, kSym>(ft, nullptr, f1t, a.P, t, C, as0, ab0, flag);
+                tube_stage<TS, 0, kEq, kSym>(ft, nullptr, f1t, a.P, t, C, as0, ab0, flag);
                 __syncthreads();
-                tube_stage<TS, 1, kDF, kSym>(f1t, ft, ft, a.P, t, C, as1, ab1, flag);
+                tube_stage<TS, 1, kEq, kSym>(f1t, ft, ft, a.P, t, C, as1, ab1, flag);
             }
             __syncthreads();
         }
@@ -415,13 +423,13 @@ __global__ void __launch_bounds__(128) batch_macros_kernel(const BatchArgs a, co
     }
 }
 
-template <typename TS, bool kDF, bool kSym>
+template <typename TS, int kEq, bool kSym>
 void *batch_func_t(int threads)
 {
     switch (threads) {
-    case 64: return (void *)batch_kernel<TS, 64, kDF, kSym>;
-    case 256: return (void *)batch_kernel<TS, 256, kDF, kSym>;
-    default: return (void *)batch_kernel<TS, 128, kDF, kSym>;
+    case 64: return (void *)batch_kernel<TS, 64, kEq, kSym>;
+    case 256: return (void *)batch_kernel<TS, 256, kEq, kSym>;
+    default: return (void *)batch_kernel<TS, 128, kEq, kSym>;
     }
 }
 
@@ -429,10 +437,12 @@ void *batch_func_t(int threads)
 void *batch_func(int precision, int threads, bool sym)
 {
     if (precision == CDBM_FP32_DF64)
-        return sym ? batch_func_t<float, true, true>(threads) : batch_func_t<float, true, false>(threads);
+        return sym ? batch_func_t<float, kEqDF, true>(threads) : batch_func_t<float, kEqDF, false>(threads);
+    if (precision == CDBM_FP32_DEV)
+        return sym ? batch_func_t<float, kEqF32, true>(threads) : batch_func_t<float, kEqF32, false>(threads);
     if (precision == CDBM_FP32_BULK)
-        return sym ? batch_func_t<float, false, true>(threads) : batch_func_t<float, false, false>(threads);
-    return sym ? batch_func_t<double, false, true>(threads) : batch_func_t<double, false, false>(threads);
+        return sym ? batch_func_t<float, kEqDouble, true>(threads) : batch_func_t<float, kEqDouble, false>(threads);
+    return sym ? batch_func_t<double, kEqDouble, true>(threads) : batch_func_t<double, kEqDouble, false>(threads);
 }
 
 }  // namespace
@@ -637,9 +647,9 @@ cdbm_status cdbm_batch_create(int ntubes, const int *nx, const double *dx, const
     if (!(std::isfinite(dt) && dt > 0 && std::isfinite(tau) && tau > 0))
         return bcreate_err(CDBM_EINVAL, "dt and tau must be finite and > 0");
     if (dt / tau > 2.0) return bcreate_err(CDBM_EINVAL, "dt/tau = %g exceeds 2", dt / tau);
-    if (precision != CDBM_FP64 && precision != CDBM_FP32_BULK && precision != CDBM_FP32_DF64)
-        return bcreate_err(CDBM_EINVAL, "unsupported precision %d (the batch takes CDBM_FP64, CDBM_FP32_BULK "
-                                        "and CDBM_FP32_DF64)", precision);
+    if (precision != CDBM_FP64 && precision != CDBM_FP32_BULK && precision != CDBM_FP32_DF64 &&
+        precision != CDBM_FP32_DEV)
+        return bcreate_err(CDBM_EINVAL, "unsupported precision %d", precision);
     double vmax = 0.0;
     for (int g = 0; g < 4; ++g) {
         if (!std::isfinite(vset->v[g]) || !std::isfinite(vset->eta[g]) || vset->v[g] <= 0 || vset->eta[g] < 0)
@@ -705,6 +715,7 @@ cdbm_status cdbm_batch_create(int ntubes, const int *nx, const double *dx, const
             }
             C.dfm = df_model(C.m);
             C.dfm2 = df_model_twice(C.dfm);
+            for (int s = 0; s < 2; ++s) C.dp[s] = dev_proj(C.m, gamma[s] * h);
         }
         TubeInfo &ti = b->info[t];
         memset(&ti, 0, sizeof(ti));

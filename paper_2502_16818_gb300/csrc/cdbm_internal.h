@@ -231,6 +231,7 @@ DFShift df_shift(const double sF[4], double rhoF, double EF);
 // Fills a.d from the double constants of a.
 void fill_df_consts(StageArgs &a);
 // The conservation projection of a stage whose blocks are scaled by gh = gamma h.
+DevProj dev_proj(const ModelConsts &m, double gh);
 void fill_dev_proj(StageArgs &a, double gh);
 // The same constants with each value twice, for the two-column (packed FP32x2) kernels.
 DFBlocksT<float2> df_blocks_twice(const DFBlocks &d);

@@ -1089,21 +1089,25 @@ void fill_df_consts(StageArgs &a)
     }
 }
 
-void fill_dev_proj(StageArgs &a, double gh)
+DevProj dev_proj(const ModelConsts &m, double gh)
 {
     double sw = 0.0, sw2 = 0.0, kc = 0.0;
     for (int g = 0; g < 4; ++g) {
-        sw += a.m.w[g];
-        sw2 += a.m.w[g] * a.m.w[g];
-        kc += ((g & 1) == 0 ? 2.0 : 4.0) * a.m.c[g] * a.m.c[g];    // sum_i c_ix^2 over the group
+        sw += m.w[g];
+        sw2 += m.w[g] * m.w[g];
+        kc += ((g & 1) == 0 ? 2.0 : 4.0) * m.c[g] * m.c[g];    // sum_i c_ix^2 over the group
     }
     const double m00 = 16.0, m01 = 4.0 * sw, m11 = 4.0 * sw2, det = m00 * m11 - m01 * m01;
-    a.dp.gh = (float)gh;
-    a.dp.a00 = (float)(m11 / det);
-    a.dp.a01 = (float)(-m01 / det);
-    a.dp.a11 = (float)(m00 / det);
-    a.dp.rkc = (float)(1.0 / kc);
+    DevProj d;
+    d.gh = (float)gh;
+    d.a00 = (float)(m11 / det);
+    d.a01 = (float)(-m01 / det);
+    d.a11 = (float)(m00 / det);
+    d.rkc = (float)(1.0 / kc);
+    return d;
 }
+
+void fill_dev_proj(StageArgs &a, double gh) { a.dp = dev_proj(a.m, gh); }
 
 cudaError_t launch_stage(const StageLaunch &L, const void *g, const void *base, void *out,
                          const StageArgs &a, unsigned *flag, cudaStream_t s)

@@ -101,16 +101,15 @@ def test_diagnostic_and_batch_switch_argument_checks(lib):
         assert st == cdbm.CDBM_EINVAL, (blocks, threads, iters)
     assert lib_.cdbm_diag_fp64_fma(None, 1, 128, 1, None, ctypes.byref(flops)) == cdbm.CDBM_EINVAL
     assert lib_.cdbm_batch_set_symmetric(None, 1) == cdbm.CDBM_EINVAL
-    # the batch refuses the single-precision deviation equilibrium of the grid API
+    # the batch validates its precision before any CUDA call
     nx = (ctypes.c_int * 1)(10)
     dx = (ctypes.c_double * 1)(0.1)
     I = (ctypes.c_double * 1)(0.0)
     vset = cdbm.cdbm_vset((ctypes.c_double * 4)(*W.VSET_SOD[0]), (ctypes.c_double * 4)(*W.VSET_SOD[1]))
     out = ctypes.c_void_p(123)
-    st = lib_.cdbm_batch_create(1, nx, dx, I, ctypes.byref(vset), 1e-4, 1e-5, cdbm.CDBM_FP32_DEV, None, None,
-                                ctypes.byref(out))
+    st = lib_.cdbm_batch_create(1, nx, dx, I, ctypes.byref(vset), 1e-4, 1e-5, 7, None, None, ctypes.byref(out))
     assert st == cdbm.CDBM_EINVAL and out.value is None
-    assert "unsupported precision 3" in lib_.cdbm_last_error(None).decode()
+    assert "unsupported precision 7" in lib_.cdbm_last_error(None).decode()
 
 
 def test_symmetric_velocity_maps(tmp_path):

@@ -1,8 +1,9 @@
-"""Batched ensembles of shock tubes (cdbm_batch_*) against the CPU oracle.
+"""Batched ensembles of shock tubes (cdbm_batch_*) against the CPU oracle, in all four
+precisions.
 
 Each tube of a batch is an independent Ny = 1 run; the oracle runs every checked
 tube on its own.  Acceptance: FP64 batch <= 1e-10 relative max-norm on rho, u, T
-(as the single-grid path); single-precision batches (FP32_BULK, FP32_DF64) <= 1e-5
+(as the single-grid path); single-precision batches (FP32_BULK, FP32_DF64, FP32_DEV) <= 1e-5
 relative L2 density error.
 The result of a batch does not depend on its tile (threads per block, partition):
 each cell's arithmetic is the same, so states agree bit for bit.
@@ -68,7 +69,7 @@ def test_batch_fp64_matches_oracle_per_tube():
         assert rel(got[3], ref[3][0]) <= 1e-10, t
 
 
-@pytest.mark.parametrize("precision", [1, 2], ids=["fp32_bulk", "fp32_df64"])
+@pytest.mark.parametrize("precision", [1, 2, 3], ids=["fp32_bulk", "fp32_df64", "fp32_dev"])
 def test_batch_single_precision_matches_oracle_per_tube(precision):
     tubes = tubes_small(seed=4)
     b, out = run_batch(tubes, 200, precision=precision)
@@ -79,7 +80,7 @@ def test_batch_single_precision_matches_oracle_per_tube(precision):
         assert l2 <= 1e-5, (t, l2)
 
 
-@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
 def test_batch_result_independent_of_tile(precision):
     tubes = tubes_small(n=40, seed=5, steps=30)
     outs = [run_batch(tubes, 30, precision, tile=tile)[1] for tile in ((64, 1), (128, 3), (256, 4))]
@@ -89,7 +90,7 @@ def test_batch_result_independent_of_tile(precision):
             assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
 def test_batch_symmetric_kernels_equal_general_kernels(precision):
     """Tubes that start with u_y = 0 stay mirror-symmetric in y; the symmetric
     kernels compute the 10 distinct velocities only and must give the general
@@ -109,7 +110,7 @@ def test_batch_symmetric_kernels_equal_general_kernels(precision):
         assert np.array_equal(a, c)
 
 
-@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
 def test_batch_tiny_tubes(precision):
     """Tubes of 1, 2, 3 and 5 cells, where every zero-gradient neighbour index is
     clamped and the two-cell df64 form has an odd last cell: the symmetric kernels
@@ -195,7 +196,7 @@ def _oracle_cached(tubes, t):
     return _ORACLE_CACHE[t]
 
 
-@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
 def test_full_ensemble_sampled_tubes(precision):
     """The configured ensemble: 1024 tubes, Nx ~ U{200..4000} (seed 0), 1000 steps,
     autotuned tile; the shortest and longest tube, one tube of each I class and eight
