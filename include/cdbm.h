@@ -148,11 +148,10 @@ cdbm_status cdbm_init(cdbm_ctx *ctx, const double *rho, const double *ux, const 
  * fused Runge-Kutta stage kernels (rho, u, T -> f_eq -> BGK + NND transport of all
  * 16 velocities -> stage update).  Launches are replayed from a CUDA graph.  A 1-D
  * grid (ny = 1) small enough for one thread-block cluster (at most 16 x 64 cells for
- * CDBM_FP64, 16 x 256 for CDBM_FP32_BULK and CDBM_FP32_DF64) instead runs all nsteps
+ * CDBM_FP64, 16 x 256 for the three single-precision states) instead runs all nsteps
  * in one persistent launch with its state in the cluster's shared memory; the
  * results are the same bit for bit for the single-precision states and the same to
  * rounding for CDBM_FP64, whose cluster kernel splits each cell over four threads.
- * CDBM_FP32_DEV steps every grid with the stage kernels.
  * Asynchronous; a non-physical state is reported by the next cdbm_sync.
  */
 cdbm_status cdbm_step(cdbm_ctx *ctx, int nsteps);
