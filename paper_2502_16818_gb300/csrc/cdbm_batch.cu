@@ -308,10 +308,13 @@ __device__ __forceinline__ void tube_stage2(const float *g, const float *base, f
 // df64 one, whose two cells of float arithmetic take about as many.  The symmetric
 // forms keep less live state: 512 for FP64 and FP32_BULK (126 / 116 registers at
 // 128 threads, no spills; 1.97e9 / 3.05e9 against 1.95e9 / 2.90e9 cell-updates/s on
-// the 1024-tube ensemble) and 640 for df64 (96 registers; 1.13e10 against 1.07e10).
+// the 1024-tube ensemble) and 640 for df64 (96 registers; 1.13e10 against 1.07e10;
+// 768 spilled 380 bytes).  The one-cell deviation equilibrium fits 64 registers
+// without spills, so 1024 (32 warps per SM): 1.50e10 against 1.31e10 at 512 (127
+// registers); 1280 spilled and fell back to 1.32e10.
 constexpr int batch_thread_budget(int eq, bool sym)
 {
-    return eq == kEqF32 ? 512 : (sym ? (eq == kEqDF ? 640 : 512) : 384);
+    return eq == kEqF32 ? 1024 : (sym ? (eq == kEqDF ? 640 : 512) : 384);
 }
 constexpr int batch_min_blocks(int threads, int eq, bool sym)
 {
