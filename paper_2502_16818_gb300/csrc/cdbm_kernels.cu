@@ -421,8 +421,8 @@ __global__ void __launch_bounds__(kStageThreads, kMarch2MinBlocks)
         // row y+2 and, in the second stage, the next base row are prefetched into L2
         // without holding registers. Row y+2 is what the downward velocities read in
         // this row and what the next row stages. On the 4096^2 vortex this took the
-        // step from 1.39 to 1.17 ms. The df64 kernel, at its register limit, did
-        // not gain.
+        // step from 1.34-1.40 to 1.09-1.17 ms (the range over GPUs). The df64
+        // kernel, at its register limit, did not gain.
         if constexpr (kEq == kEqF32) {
 #pragma unroll
             for (int i = 0; i < kNV; ++i) prefetch_l2(g + i * P + rp2 + x0);
